@@ -1,0 +1,200 @@
+/*
+ * sfmm.h -- C ABI of the GB300 solid-harmonic translation library.
+ *
+ * Batched M2M, M2L and L2L translations of solid-harmonic expansions for the
+ * Laplace kernel 1/|x-y| (Kirchhart, "solidfmm: A highly optimised library of
+ * operations on the solid harmonics for use in fast multipole methods",
+ * arXiv 2202.02847).  Every translation is computed by the rotation-based
+ * factorisation of Sec. 2.4 / Sec. 3.4: scale the shift to unit length
+ * (eq. scaling), rotate about z, swap x and z (Dehnen's matrices, eq.
+ * swaptransform, in the reduced real form of eq. FGmappings), rotate about z,
+ * swap again, translate along the z axis in O(P^3) (eq. zm2lkernels for M2L),
+ * and undo the change of coordinates.  Kernels are hand-written CUDA for
+ * sm_103a (GB300) and run asynchronously on the caller's stream.
+ *
+ * ------------------------------------------------------------------ data
+ * Solid (Sec. 2.1, Fig. 1).  An expansion of order P has coefficients
+ * C_n^m, 0 <= n < P, |m| <= n, with C_n^{-m} = (-1)^m conj(C_n^m); only m >= 0
+ * is stored, Im C_n^0 is stored as 0.  A solid is P(P+1) contiguous reals
+ * (double for SFMM_F64 handles, float for SFMM_F32): row n occupies reals
+ * [n(n+1), (n+1)(n+2)) as  Re C_n^0 .. Re C_n^n, Im C_n^0 .. Im C_n^n.
+ * (The paper's Fig. 1 gives the positions in a figure that is not available;
+ * this row-wise Re/Im split is the layout its swap buffers use, Sec. 3.3.)
+ *
+ * Expansions (Sec. 2.1, eq. MLexpansions):
+ *   multipole about x_A:  phi(x) = sum_{n,m} M_n^m conj(S_n^m(x - x_A))
+ *   local about x_B:      phi(x) = sum_{n,m} L_n^m conj(R_n^m(x - x_B))
+ * with R, S the regular and singular harmonics of the Appendix (no
+ * Condon-Shortley phase; R_n^m = r^n P_n^m(cos t) e^{im p}/(n+m)!,
+ * S_n^m = (n-m)! P_n^m(cos t) e^{im p}/r^{n+1}).
+ *
+ * Shift vectors are 3 reals (x, y, z) of the handle's dtype:
+ *   r = (centre of the output expansion) - (centre of the input expansion),
+ * i.e. r = x_B - x_A for M2L (Sec. 2.1, r_AB).  M2L needs r != 0 and the
+ * expansions well separated; M2M and L2L with r = 0 copy the input.
+ *
+ * Orders (Sec. 1.1, mixed-order translations): the input has order p_in and
+ * the output order p_out, 1 <= p_in, p_out <= P_max of the handle.  M2L is the
+ * double-height kernel (Sec. 2.1, eq. m2lkernels, right): every output
+ * coefficient depends on every input coefficient.
+ *
+ * -------------------------------------------------------------- semantics
+ * All pointers passed to the *_batch / *_lists calls are DEVICE pointers; the
+ * caller owns every array and keeps it alive until the stream reaches the
+ * work.  Calls enqueue work on `stream` and return without synchronising.
+ * Host-detectable errors are returned synchronously and enqueue nothing;
+ * errors found by a kernel are recorded in the handle's device status word,
+ * read (and cleared) by sfmm_sync_status().  No C++ exception crosses this
+ * interface.  A handle is immutable after sfmm_create and may be used from
+ * several host threads and streams at once (Sec. 1.1, thread safe).
+ * count = 0 is a no-op returning SFMM_OK.
+ */
+#ifndef SFMM_H
+#define SFMM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *sfmm_stream; /* = cudaStream_t; NULL = legacy default stream */
+
+typedef struct sfmm_ctx *sfmm_handle;
+
+typedef enum { SFMM_F32 = 0, SFMM_F64 = 1 } sfmm_dtype;
+
+typedef enum {
+    SFMM_OK = 0,
+    SFMM_ERR_ARG = 1,          /* null pointer, negative count, bad enum       */
+    SFMM_ERR_ORDER = 2,        /* p_in / p_out outside [1, P_max]              */
+    SFMM_ERR_NOMEM = 3,        /* device or host allocation failed             */
+    SFMM_ERR_CUDA = 4,         /* a CUDA runtime call failed                   */
+    SFMM_ERR_TIMEOUT = 5,      /* a bounded device wait gave up                */
+    SFMM_ERR_UNSUPPORTED = 6,  /* valid request this build cannot serve        */
+    SFMM_ERR_DEVICE = 7        /* a kernel rejected its input (status word)    */
+} sfmm_status;
+
+typedef enum { SFMM_M2M = 0, SFMM_M2L = 1, SFMM_L2L = 2 } sfmm_op;
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char *sfmm_status_string(sfmm_status s);
+
+/*
+ * Precomputation (Sec. 3.1): build the tables for orders up to P_max on the
+ * current CUDA device and return a handle owning them.
+ *   - Dehnen's swap matrices B_n (Appendix recurrence, computed exactly: every
+ *     entry is an integer over 2^n), brought to the orthonormal basis
+ *     Rhat = R sqrt((n-m)!(n+m)!), Shat = S / sqrt((n-m)!(n+m)!), where one
+ *     symmetric orthogonal matrix serves both the M and the L side, then
+ *     reduced to the real chequerboard matrices F_n, G_n (eq. FGmappings,
+ *     Fig. 2) and packed without their structural zeros;
+ *   - the z-axis translation matrices of M2L (eq. zm2l-matrix, factorials),
+ *     M2M and L2L in the same basis.
+ * 1 <= P_max <= 64 for SFMM_F64; 1 <= P_max <= 29 for SFMM_F32 (the FP32
+ * range of the basis factors sqrt((n-m)!(n+m)!)).  Synchronous.
+ * Errors: SFMM_ERR_ARG (out == NULL, bad dtype), SFMM_ERR_ORDER (P_max),
+ * SFMM_ERR_NOMEM, SFMM_ERR_CUDA.  On error *out is set to NULL.
+ */
+sfmm_status sfmm_create(int P_max, sfmm_dtype dtype, sfmm_handle *out);
+
+/* Release a handle (synchronises the device first).  NULL is accepted. */
+sfmm_status sfmm_destroy(sfmm_handle h);
+
+/* P_max and dtype of a handle (either output pointer may be NULL). */
+sfmm_status sfmm_get_info(sfmm_handle h, int *P_max, sfmm_dtype *dtype);
+
+/*
+ * Batched translations (Sec. 3.4 for M2L; M2M and L2L are the variants the
+ * paper implements but does not print, Sec. 1.2).  For i < count:
+ *   out[i]  = T(in[i], shift[3i..3i+2])          (accumulate == 0)
+ *   out[i] += T(in[i], shift[3i..3i+2])          (accumulate != 0)
+ * with T = M2M, M2L or L2L from order p_in to order p_out:
+ *   M2M: M'_n^m = sum_{k<=n} sum_l M_k^l R_{n-k}^{m-l}(-r)
+ *   M2L: L_n^m  = (-1)^n sum_{k<p_in} sum_l conj(M_k^l) S_{n+k}^{m+l}(r)
+ *   L2L: L'_n^m = sum_{k>=n} sum_l L_k^l conj(R_{k-n}^{l-m}(r))
+ * in  : device array of `count` device pointers, each to a solid of order p_in
+ * out : device array of `count` device pointers, each to a solid of order p_out;
+ *       within one call the out[i] must not overlap each other or any in[j]
+ *       (each output receives exactly one result per call).
+ * shift: device array of 3*count reals (handle dtype), r = new - old centre.
+ * Solids must be aligned to the element size.  One GPU thread computes one
+ * translation; results do not depend on the batch they are computed in.
+ * Errors: SFMM_ERR_ARG, SFMM_ERR_ORDER, SFMM_ERR_UNSUPPORTED, SFMM_ERR_CUDA.
+ */
+sfmm_status sfmm_m2m_batch(sfmm_handle h, const void *const *in, void *const *out,
+                           const void *shift, int p_in, int p_out, long long count,
+                           int accumulate, sfmm_stream stream);
+sfmm_status sfmm_m2l_batch(sfmm_handle h, const void *const *in, void *const *out,
+                           const void *shift, int p_in, int p_out, long long count,
+                           int accumulate, sfmm_stream stream);
+sfmm_status sfmm_l2l_batch(sfmm_handle h, const void *const *in, void *const *out,
+                           const void *shift, int p_in, int p_out, long long count,
+                           int accumulate, sfmm_stream stream);
+
+/*
+ * Interaction lists (target-major CSR), the form an FMM pass uses: for every
+ * target t < n_targets,
+ *   out[t] (+)= sum_{j = offsets[t]}^{offsets[t+1]-1} T(src[j], shift[3j..3j+2])
+ * summed in list order j (deterministic: the same lists give bitwise the same
+ * result on every run).  With accumulate == 0 out[t] is overwritten (a target
+ * with an empty list receives zeros).
+ * src    : device array of nnz = offsets[n_targets] device pointers (order p_in)
+ * shift  : device array of 3*nnz reals, r = target centre - source centre
+ * offsets: device array of n_targets+1 non-decreasing long long, offsets[0] = 0
+ * out    : device array of n_targets distinct device pointers (order p_out),
+ *          not overlapping any source
+ * One GPU thread owns one target; targets whose lists have similar lengths
+ * should be adjacent (the FMM planner sorts them) so that the threads of a
+ * warp finish together.
+ * Errors: as for the batch calls.
+ */
+sfmm_status sfmm_translate_lists(sfmm_handle h, sfmm_op op, const void *const *src,
+                                 const void *shift, const long long *offsets,
+                                 void *const *out, int p_in, int p_out,
+                                 long long n_targets, int accumulate, sfmm_stream stream);
+
+/*
+ * Particle-to-expansion helpers (not part of the paper's translation library;
+ * they build inputs on the device).  Points are sorted by box: box b owns
+ * points [offsets[b], offsets[b+1]).  For every box b < n_boxes:
+ *   P2M: out_b = sum_j q_j R_n^m(y_j - centre_b)   (multipole, order P)
+ *   P2L: out_b = sum_j q_j S_n^m(y_j - centre_b)   (local, order P)
+ * (eq. MLexpansions with the addition theorem 1/|x-y| = sum R(y) conj(S(x))).
+ * points: device, 3*N reals; q: device, N reals; offsets: device, n_boxes+1;
+ * centres: device, 3*n_boxes reals; out: device, n_boxes solids of order P
+ * stored contiguously with stride P(P+1) reals (overwritten).
+ */
+sfmm_status sfmm_p2m_boxes(sfmm_handle h, int P, const void *points, const void *q,
+                           const long long *offsets, const void *centres, void *out,
+                           long long n_boxes, sfmm_stream stream);
+sfmm_status sfmm_p2l_boxes(sfmm_handle h, int P, const void *points, const void *q,
+                           const long long *offsets, const void *centres, void *out,
+                           long long n_boxes, sfmm_stream stream);
+
+/*
+ * Read and clear the handle's device status word after `stream` has drained
+ * (synchronises the stream).  *device_status receives the raw word (0 = no
+ * kernel reported an error); returns SFMM_ERR_DEVICE if it was non-zero.
+ */
+sfmm_status sfmm_sync_status(sfmm_handle h, sfmm_stream stream, int *device_status);
+
+/*
+ * Host-side introspection of the precomputed tables (no GPU, no handle).
+ * sfmm_host_swap_matrices: the dense reduced swap matrices F_n and G_n of
+ * eq. FGmappings in the orthonormal basis (row m, column l, (n+1)^2 doubles
+ * each; the chequerboard zeros of Fig. 2 are stored as exact zeros), the
+ * matrices every swap step of every translation applies.  0 <= n <= 63.
+ * sfmm_host_ztranslate: the dense z-axis translation block of column m for op
+ * at order P ((P-m)^2 doubles, row n-m, column k-m, orthonormal basis; for M2L
+ * eq. zm2lkernels (double height) with factorials (n+k)!, eq. zm2l-matrix).
+ * Errors: SFMM_ERR_ARG (null output, bad op), SFMM_ERR_ORDER (n, P, m range).
+ */
+sfmm_status sfmm_host_swap_matrices(int n, double *F, double *G);
+sfmm_status sfmm_host_ztranslate(sfmm_op op, int P, int m, double *T);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFMM_H */

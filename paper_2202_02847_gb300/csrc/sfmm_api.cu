@@ -1,0 +1,444 @@
+// C ABI of the translation library: handle, argument validation, launches.
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "sfmm.h"
+#include "sfmm_kernels.cuh"
+#include "sfmm_tables.h"
+
+using namespace sfmm;
+
+struct sfmm_ctx {
+    int Pmax = 0;
+    sfmm_dtype dtype = SFMM_F64;
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;      // max dynamic shared memory per block
+    void *d_tables = nullptr;   // one allocation holding every table
+    int *d_status = nullptr;    // device status word (atomicOr by kernels)
+    DevTables<double> t64{};
+    DevTables<float> t32{};
+    // global scratch for orders whose rotated solid does not fit in shared
+    // memory: one slot of x_elems(P_max) elements per lane of a resident warp
+    void *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    // launches that use the scratch are ordered through this event so that
+    // calls on different streams never share it concurrently
+    std::mutex scratch_mu;
+    cudaEvent_t scratch_free = nullptr;
+};
+
+namespace {
+
+constexpr int kMaxPmax64 = 64;
+constexpr int kMaxPmax32 = 29;
+
+template <typename T, bool XG>
+void set_attrs_one(size_t smem) {
+    cudaFuncSetAttribute(batch_kernel<T, OP_M2M, XG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(batch_kernel<T, OP_M2L, XG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(batch_kernel<T, OP_L2L, XG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(lists_kernel<T, OP_M2M, XG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(lists_kernel<T, OP_M2L, XG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(lists_kernel<T, OP_L2L, XG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename T>
+void set_kernel_attrs(size_t smem) {
+    set_attrs_one<T, false>(smem);
+    set_attrs_one<T, true>(smem);
+    cudaFuncSetAttribute(p2x_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(p2x_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// Copy the host tables into one device buffer converted to T.
+template <typename T>
+sfmm_status upload(const HostTables &ht, sfmm_ctx *h, DevTables<T> *dt) {
+    const size_t nF = ht.F.size(), nG = ht.G.size(), nc = ht.c.size(), nT = ht.Tz[0].size();
+    const size_t nreal = nF + nG + 2 * nc + 3 * nT;
+    const size_t nint = 2 * (size_t)(ht.Pmax + 1);
+    const size_t bytes = nreal * sizeof(T) + nint * sizeof(int) + 256;
+    std::vector<unsigned char> host(bytes, 0);
+    T *r = reinterpret_cast<T *>(host.data());
+    size_t o = 0;
+    auto put = [&](const std::vector<double> &v) {
+        const size_t at = o;
+        for (size_t i = 0; i < v.size(); ++i) r[o + i] = (T)v[i];
+        o += v.size();
+        return at;
+    };
+    const size_t oF = put(ht.F), oG = put(ht.G), oc = put(ht.c), oic = put(ht.ic);
+    const size_t oT0 = put(ht.Tz[0]), oT1 = put(ht.Tz[1]), oT2 = put(ht.Tz[2]);
+    size_t ibyte = (o * sizeof(T) + 15) / 16 * 16;
+    int *ip = reinterpret_cast<int *>(host.data() + ibyte);
+    std::memcpy(ip, ht.Frow.data(), (ht.Pmax + 1) * sizeof(int));
+    std::memcpy(ip + ht.Pmax + 1, ht.Grow.data(), (ht.Pmax + 1) * sizeof(int));
+    if (cudaMalloc(&h->d_tables, bytes) != cudaSuccess) return SFMM_ERR_NOMEM;
+    if (cudaMemcpy(h->d_tables, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+        return SFMM_ERR_CUDA;
+    const T *d = reinterpret_cast<const T *>(h->d_tables);
+    const int *di = reinterpret_cast<const int *>(static_cast<unsigned char *>(h->d_tables) + ibyte);
+    dt->F = d + oF;
+    dt->G = d + oG;
+    dt->c = d + oc;
+    dt->ic = d + oic;
+    dt->Tz[0] = d + oT0;
+    dt->Tz[1] = d + oT1;
+    dt->Tz[2] = d + oT2;
+    dt->Frow = di;
+    dt->Grow = di + ht.Pmax + 1;
+    dt->Pmax = ht.Pmax;
+    return SFMM_OK;
+}
+
+sfmm_status check_common(sfmm_handle h, int p_in, int p_out, long long count) {
+    if (h == nullptr || count < 0) return SFMM_ERR_ARG;
+    if (p_in < 1 || p_out < 1 || p_in > h->Pmax || p_out > h->Pmax) return SFMM_ERR_ORDER;
+    return SFMM_OK;
+}
+
+// Launch geometry of one translation call.
+struct Geometry {
+    bool xg = false;        // rotated solid in global scratch
+    int warps = 0;          // warps per block
+    size_t smem = 0;        // dynamic shared memory per block
+    long long blocks = 0;
+};
+
+template <typename T>
+bool shared_only_fits(const sfmm_ctx *h, int p_in, int p_out) {
+    return (size_t)(x_elems(p_in) + row_elems(p_in, p_out)) * WARP * sizeof(T) <= h->smem_optin;
+}
+
+template <typename T>
+Geometry pick_geometry(const sfmm_ctx *h, int p_in, int p_out, long long units) {
+    Geometry g;
+    const size_t sz = sizeof(T);
+    if (shared_only_fits<T>(h, p_in, p_out)) {
+        const size_t per_warp = (size_t)(x_elems(p_in) + row_elems(p_in, p_out)) * WARP * sz;
+        // aim for two resident blocks per SM (half the opt-in budget each)
+        int w = (int)(h->smem_optin / 2 / per_warp);
+        if (w < 1) w = 1;
+        if (w > 8) w = 8;
+        g.warps = w;
+        g.smem = (size_t)w * per_warp;
+        g.blocks = (units + w * WARP - 1) / (w * WARP);
+        return g;
+    }
+    const size_t per_warp = (size_t)row_elems(p_in, p_out) * WARP * sz;
+    const size_t slot = (size_t)x_elems(p_in) * WARP * sz;
+    if (h->d_scratch == nullptr || per_warp > h->smem_optin) return g;   // warps = 0
+    int w = (int)(h->smem_optin / 2 / per_warp);
+    if (w < 1) w = 1;
+    if (w > 4) w = 4;
+    const long long slots = (long long)(h->scratch_bytes / slot);
+    long long blocks = slots / w;
+    const long long need = (units + w * WARP - 1) / (w * WARP);
+    if (blocks > need) blocks = need;
+    if (blocks < 1) return g;
+    g.xg = true;
+    g.warps = w;
+    g.smem = (size_t)w * per_warp;
+    g.blocks = blocks;
+    return g;
+}
+
+// Order a scratch-using launch after the previous one (any stream).
+struct ScratchGuard {
+    sfmm_ctx *h;
+    cudaStream_t s;
+    bool on;
+    std::unique_lock<std::mutex> lk;
+    ScratchGuard(sfmm_ctx *h_, cudaStream_t s_, bool on_) : h(h_), s(s_), on(on_) {
+        if (!on) return;
+        lk = std::unique_lock<std::mutex>(h->scratch_mu);
+        cudaStreamWaitEvent(s, h->scratch_free, 0);
+    }
+    ~ScratchGuard() {
+        if (on) cudaEventRecord(h->scratch_free, s);
+    }
+};
+
+template <typename T, int OP>
+void batch_launch(const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
+                  const T *const *I, T *const *O, const T *S, int p_in, int p_out,
+                  long long count, int acc, T *scratch, int *status) {
+    if (g.xg)
+        batch_kernel<T, OP, true><<<(unsigned)g.blocks, g.warps * WARP, g.smem, stream>>>(tb, I, O, S, p_in, p_out, count, acc, scratch, status);
+    else
+        batch_kernel<T, OP, false><<<(unsigned)g.blocks, g.warps * WARP, g.smem, stream>>>(tb, I, O, S, p_in, p_out, count, acc, scratch, status);
+}
+
+template <typename T, int OP>
+void lists_launch(const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
+                  const T *const *Sp, const T *S, const long long *offsets, T *const *O,
+                  int p_in, int p_out, long long nt, int acc, T *scratch, int *status) {
+    if (g.xg)
+        lists_kernel<T, OP, true><<<(unsigned)g.blocks, g.warps * WARP, g.smem, stream>>>(tb, Sp, S, offsets, O, p_in, p_out, nt, acc, scratch, status);
+    else
+        lists_kernel<T, OP, false><<<(unsigned)g.blocks, g.warps * WARP, g.smem, stream>>>(tb, Sp, S, offsets, O, p_in, p_out, nt, acc, scratch, status);
+}
+
+template <typename T>
+sfmm_status launch_batch(sfmm_handle h, int op, const void *const *in, void *const *out,
+                         const void *shift, int p_in, int p_out, long long count,
+                         int accumulate, cudaStream_t stream, const DevTables<T> &tb) {
+    const Geometry g = pick_geometry<T>(h, p_in, p_out, count);
+    if (g.warps < 1) return SFMM_ERR_UNSUPPORTED;
+    if (g.blocks > 0x7fffffffLL) return SFMM_ERR_UNSUPPORTED;
+    auto I = reinterpret_cast<const T *const *>(in);
+    auto O = reinterpret_cast<T *const *>(out);
+    auto S = reinterpret_cast<const T *>(shift);
+    T *scr = reinterpret_cast<T *>(h->d_scratch);
+    ScratchGuard guard(h, stream, g.xg);
+    if (op == OP_M2M) batch_launch<T, OP_M2M>(g, stream, tb, I, O, S, p_in, p_out, count, accumulate, scr, h->d_status);
+    else if (op == OP_M2L) batch_launch<T, OP_M2L>(g, stream, tb, I, O, S, p_in, p_out, count, accumulate, scr, h->d_status);
+    else batch_launch<T, OP_L2L>(g, stream, tb, I, O, S, p_in, p_out, count, accumulate, scr, h->d_status);
+    return cudaGetLastError() == cudaSuccess ? SFMM_OK : SFMM_ERR_CUDA;
+}
+
+template <typename T>
+sfmm_status launch_lists(sfmm_handle h, int op, const void *const *src, const void *shift,
+                         const long long *offsets, void *const *out, int p_in, int p_out,
+                         long long n_targets, int accumulate, cudaStream_t stream,
+                         const DevTables<T> &tb) {
+    const Geometry g = pick_geometry<T>(h, p_in, p_out, n_targets);
+    if (g.warps < 1) return SFMM_ERR_UNSUPPORTED;
+    if (g.blocks > 0x7fffffffLL) return SFMM_ERR_UNSUPPORTED;
+    auto Sp = reinterpret_cast<const T *const *>(src);
+    auto O = reinterpret_cast<T *const *>(out);
+    auto S = reinterpret_cast<const T *>(shift);
+    T *scr = reinterpret_cast<T *>(h->d_scratch);
+    ScratchGuard guard(h, stream, g.xg);
+    if (op == OP_M2M) lists_launch<T, OP_M2M>(g, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, scr, h->d_status);
+    else if (op == OP_M2L) lists_launch<T, OP_M2L>(g, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, scr, h->d_status);
+    else lists_launch<T, OP_L2L>(g, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, scr, h->d_status);
+    return cudaGetLastError() == cudaSuccess ? SFMM_OK : SFMM_ERR_CUDA;
+}
+
+template <typename T>
+sfmm_status launch_p2x(sfmm_handle h, bool singular, int P, const void *points, const void *q,
+                       const long long *offsets, const void *centres, void *out,
+                       long long n_boxes, cudaStream_t stream) {
+    const size_t per_warp = (size_t)2 * P * (P + 1) * WARP * sizeof(T);
+    int w = (int)(h->smem_optin / 2 / per_warp);
+    if (w < 1) w = (int)(h->smem_optin / per_warp);
+    if (w < 1) return SFMM_ERR_UNSUPPORTED;
+    if (w > 4) w = 4;
+    const int threads = w * WARP;
+    const long long blocks = (n_boxes + threads - 1) / threads;
+    if (blocks > 0x7fffffffLL) return SFMM_ERR_UNSUPPORTED;
+    const size_t smem = (size_t)w * per_warp;
+    auto Pt = reinterpret_cast<const T *>(points);
+    auto Q = reinterpret_cast<const T *>(q);
+    auto C = reinterpret_cast<const T *>(centres);
+    auto O = reinterpret_cast<T *>(out);
+    if (singular)
+        p2x_kernel<T, true><<<(unsigned)blocks, threads, smem, stream>>>(P, Pt, Q, offsets, C, O, n_boxes, h->d_status);
+    else
+        p2x_kernel<T, false><<<(unsigned)blocks, threads, smem, stream>>>(P, Pt, Q, offsets, C, O, n_boxes, h->d_status);
+    return cudaGetLastError() == cudaSuccess ? SFMM_OK : SFMM_ERR_CUDA;
+}
+
+sfmm_status batch(sfmm_handle h, int op, const void *const *in, void *const *out,
+                  const void *shift, int p_in, int p_out, long long count, int accumulate,
+                  sfmm_stream stream) {
+    sfmm_status st = check_common(h, p_in, p_out, count);
+    if (st != SFMM_OK) return st;
+    if (count == 0) return SFMM_OK;
+    if (in == nullptr || out == nullptr || shift == nullptr) return SFMM_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (h->dtype == SFMM_F64)
+        return launch_batch<double>(h, op, in, out, shift, p_in, p_out, count, accumulate, s, h->t64);
+    return launch_batch<float>(h, op, in, out, shift, p_in, p_out, count, accumulate, s, h->t32);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sfmm_status_string(sfmm_status s) {
+    switch (s) {
+        case SFMM_OK: return "SFMM_OK";
+        case SFMM_ERR_ARG: return "SFMM_ERR_ARG: invalid argument";
+        case SFMM_ERR_ORDER: return "SFMM_ERR_ORDER: expansion order out of range";
+        case SFMM_ERR_NOMEM: return "SFMM_ERR_NOMEM: allocation failed";
+        case SFMM_ERR_CUDA: return "SFMM_ERR_CUDA: CUDA runtime error";
+        case SFMM_ERR_TIMEOUT: return "SFMM_ERR_TIMEOUT: bounded device wait gave up";
+        case SFMM_ERR_UNSUPPORTED: return "SFMM_ERR_UNSUPPORTED: request not supported by this build";
+        case SFMM_ERR_DEVICE: return "SFMM_ERR_DEVICE: a kernel reported invalid input";
+    }
+    return "SFMM_ERR_?: unknown status";
+}
+
+sfmm_status sfmm_create(int P_max, sfmm_dtype dtype, sfmm_handle *out) {
+    if (out == nullptr) return SFMM_ERR_ARG;
+    *out = nullptr;
+    if (dtype != SFMM_F64 && dtype != SFMM_F32) return SFMM_ERR_ARG;
+    const int lim = dtype == SFMM_F64 ? kMaxPmax64 : kMaxPmax32;
+    if (P_max < 1 || P_max > lim) return SFMM_ERR_ORDER;
+    sfmm_ctx *h = new (std::nothrow) sfmm_ctx;
+    if (h == nullptr) return SFMM_ERR_NOMEM;
+    h->Pmax = P_max;
+    h->dtype = dtype;
+    int dev = 0, smc = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smc, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        delete h;
+        return SFMM_ERR_CUDA;
+    }
+    h->device = dev;
+    h->sm_count = smc;
+    h->smem_optin = (size_t)optin;
+    HostTables ht;
+    try {
+        if (build_tables(P_max, &ht) != 0) { delete h; return SFMM_ERR_ORDER; }
+    } catch (...) {
+        delete h;
+        return SFMM_ERR_NOMEM;
+    }
+    sfmm_status st = dtype == SFMM_F64 ? upload<double>(ht, h, &h->t64) : upload<float>(ht, h, &h->t32);
+    if (st == SFMM_OK && cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess) st = SFMM_ERR_NOMEM;
+    if (st == SFMM_OK && cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) st = SFMM_ERR_CUDA;
+    if (st == SFMM_OK) {
+        const size_t esz = dtype == SFMM_F64 ? sizeof(double) : sizeof(float);
+        const bool fits = (size_t)(x_elems(P_max) + row_elems(P_max, P_max)) * WARP * esz <= h->smem_optin;
+        if (!fits) {
+            // four resident warps per SM, one slot per lane
+            h->scratch_bytes = (size_t)smc * 4 * WARP * x_elems(P_max) * esz;
+            if (cudaMalloc(&h->d_scratch, h->scratch_bytes) != cudaSuccess) st = SFMM_ERR_NOMEM;
+            else if (cudaEventCreateWithFlags(&h->scratch_free, cudaEventDisableTiming) != cudaSuccess)
+                st = SFMM_ERR_CUDA;
+        }
+    }
+    if (st == SFMM_OK) {
+        if (dtype == SFMM_F64) set_kernel_attrs<double>(h->smem_optin);
+        else set_kernel_attrs<float>(h->smem_optin);
+        if (cudaGetLastError() != cudaSuccess) st = SFMM_ERR_CUDA;
+    }
+    if (st != SFMM_OK) {
+        cudaFree(h->d_tables);
+        cudaFree(h->d_status);
+        cudaFree(h->d_scratch);
+        if (h->scratch_free) cudaEventDestroy(h->scratch_free);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return SFMM_OK;
+}
+
+sfmm_status sfmm_destroy(sfmm_handle h) {
+    if (h == nullptr) return SFMM_OK;
+    cudaDeviceSynchronize();
+    cudaFree(h->d_tables);
+    cudaFree(h->d_status);
+    cudaFree(h->d_scratch);
+    if (h->scratch_free) cudaEventDestroy(h->scratch_free);
+    delete h;
+    return SFMM_OK;
+}
+
+sfmm_status sfmm_get_info(sfmm_handle h, int *P_max, sfmm_dtype *dtype) {
+    if (h == nullptr) return SFMM_ERR_ARG;
+    if (P_max) *P_max = h->Pmax;
+    if (dtype) *dtype = h->dtype;
+    return SFMM_OK;
+}
+
+sfmm_status sfmm_m2m_batch(sfmm_handle h, const void *const *in, void *const *out,
+                           const void *shift, int p_in, int p_out, long long count,
+                           int accumulate, sfmm_stream stream) {
+    return batch(h, OP_M2M, in, out, shift, p_in, p_out, count, accumulate, stream);
+}
+
+sfmm_status sfmm_m2l_batch(sfmm_handle h, const void *const *in, void *const *out,
+                           const void *shift, int p_in, int p_out, long long count,
+                           int accumulate, sfmm_stream stream) {
+    return batch(h, OP_M2L, in, out, shift, p_in, p_out, count, accumulate, stream);
+}
+
+sfmm_status sfmm_l2l_batch(sfmm_handle h, const void *const *in, void *const *out,
+                           const void *shift, int p_in, int p_out, long long count,
+                           int accumulate, sfmm_stream stream) {
+    return batch(h, OP_L2L, in, out, shift, p_in, p_out, count, accumulate, stream);
+}
+
+sfmm_status sfmm_translate_lists(sfmm_handle h, sfmm_op op, const void *const *src,
+                                 const void *shift, const long long *offsets,
+                                 void *const *out, int p_in, int p_out,
+                                 long long n_targets, int accumulate, sfmm_stream stream) {
+    sfmm_status st = check_common(h, p_in, p_out, n_targets);
+    if (st != SFMM_OK) return st;
+    if (op != SFMM_M2M && op != SFMM_M2L && op != SFMM_L2L) return SFMM_ERR_ARG;
+    if (n_targets == 0) return SFMM_OK;
+    if (src == nullptr || shift == nullptr || offsets == nullptr || out == nullptr) return SFMM_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (h->dtype == SFMM_F64)
+        return launch_lists<double>(h, (int)op, src, shift, offsets, out, p_in, p_out, n_targets, accumulate, s, h->t64);
+    return launch_lists<float>(h, (int)op, src, shift, offsets, out, p_in, p_out, n_targets, accumulate, s, h->t32);
+}
+
+static sfmm_status p2x(sfmm_handle h, bool singular, int P, const void *points, const void *q,
+                       const long long *offsets, const void *centres, void *out,
+                       long long n_boxes, sfmm_stream stream) {
+    sfmm_status st = check_common(h, P, P, n_boxes);
+    if (st != SFMM_OK) return st;
+    if (n_boxes == 0) return SFMM_OK;
+    if (points == nullptr || q == nullptr || offsets == nullptr || centres == nullptr || out == nullptr)
+        return SFMM_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (h->dtype == SFMM_F64)
+        return launch_p2x<double>(h, singular, P, points, q, offsets, centres, out, n_boxes, s);
+    return launch_p2x<float>(h, singular, P, points, q, offsets, centres, out, n_boxes, s);
+}
+
+sfmm_status sfmm_p2m_boxes(sfmm_handle h, int P, const void *points, const void *q,
+                           const long long *offsets, const void *centres, void *out,
+                           long long n_boxes, sfmm_stream stream) {
+    return p2x(h, false, P, points, q, offsets, centres, out, n_boxes, stream);
+}
+
+sfmm_status sfmm_p2l_boxes(sfmm_handle h, int P, const void *points, const void *q,
+                           const long long *offsets, const void *centres, void *out,
+                           long long n_boxes, sfmm_stream stream) {
+    return p2x(h, true, P, points, q, offsets, centres, out, n_boxes, stream);
+}
+
+sfmm_status sfmm_sync_status(sfmm_handle h, sfmm_stream stream, int *device_status) {
+    if (h == nullptr) return SFMM_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int v = 0;
+    if (cudaMemcpyAsync(&v, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return SFMM_ERR_CUDA;
+    if (v != 0 && cudaMemsetAsync(h->d_status, 0, sizeof(int), s) != cudaSuccess) return SFMM_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SFMM_ERR_CUDA;
+    if (device_status) *device_status = v;
+    return v == 0 ? SFMM_OK : SFMM_ERR_DEVICE;
+}
+
+sfmm_status sfmm_host_swap_matrices(int n, double *F, double *G) {
+    if (F == nullptr || G == nullptr) return SFMM_ERR_ARG;
+    if (n < 0 || n > 63) return SFMM_ERR_ORDER;
+    return dense_swap_matrices(n, F, G) == 0 ? SFMM_OK : SFMM_ERR_ORDER;
+}
+
+sfmm_status sfmm_host_ztranslate(sfmm_op op, int P, int m, double *T) {
+    if (T == nullptr || (op != SFMM_M2M && op != SFMM_M2L && op != SFMM_L2L)) return SFMM_ERR_ARG;
+    if (P < 1 || P > 64 || m < 0 || m >= P) return SFMM_ERR_ORDER;
+    HostTables ht;
+    if (build_tables(P, &ht) != 0) return SFMM_ERR_ORDER;
+    const long long base = ztrans_block_offset(P, m);
+    const size_t n = (size_t)(P - m) * (P - m);
+    std::memcpy(T, ht.Tz[op].data() + base, n * sizeof(double));
+    return SFMM_OK;
+}
+
+}  // extern "C"

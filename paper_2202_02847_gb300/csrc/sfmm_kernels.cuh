@@ -1,0 +1,341 @@
+// Device kernels of the rotation-based translations (Sec. 2.4, Sec. 3.4).
+//
+// Design: one GPU thread computes one translation from start to finish, the
+// way the paper lays nu solids side by side in SIMD lanes (Sec. 3.2); a warp
+// therefore runs 32 translations in lock-step with identical control flow
+// and no idle lanes.  Each thread keeps its rotated solid, two row buffers and
+// the powers of e^{i alpha}, e^{i beta} in shared memory, interleaved across
+// the 32 lanes of its warp (element e of lane j at word e*32 + j), so every
+// shared access of a warp is conflict-free.  The shared tables (swap
+// matrices, z-translation matrices, basis factors) are read from global
+// memory through L1 with warp-uniform addresses (one broadcast per warp).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sfmm_tables.h"
+
+namespace sfmm {
+
+template <typename T>
+struct DevTables {
+    const T *F, *G;          // packed reduced swap matrices (see sfmm_tables.h)
+    const int *Frow, *Grow;  // row starts, Pmax+1 each
+    const T *c, *ic;         // sqrt((n-m)!(n+m)!) and its inverse, n(n+1)/2+m
+    const T *Tz[3];          // z-axis translation blocks per op
+    int Pmax;
+};
+
+// status bits written by kernels (atomicOr into the handle's status word)
+enum { STATUS_NULL_POINTER = 1, STATUS_BAD_OFFSETS = 2 };
+
+constexpr int WARP = 32;
+
+// per-thread working set in elements for (p_in, p_out): the rotated solid
+// (x_elems) and the row buffers with the rotation powers (row_elems)
+__host__ __device__ inline int x_elems(int p_in) { return p_in * (p_in + 1); }
+__host__ __device__ inline int row_elems(int p_in, int p_out) {
+    return 8 * (p_in > p_out ? p_in : p_out);
+}
+
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double sqrt_t(double a) { return sqrt(a); }
+__device__ __forceinline__ float sqrt_t(float a) { return sqrtf(a); }
+
+template <typename T>
+__device__ __forceinline__ T ldt(const T *p) { return __ldg(p); }
+
+// Lane-strided view: element e lives at base[e * WARP].
+template <typename T>
+struct LaneArr {
+    T *p;
+    __device__ __forceinline__ T &operator[](int e) const { return p[e * WARP]; }
+    __device__ __forceinline__ LaneArr operator+(int e) const { return LaneArr{p + e * WARP}; }
+};
+
+// One axis swap of row n (eq. Mswapxz / FGmappings):
+//   Re out_m = sum_l F_n[m][l] Re in_l,   Im out_m = sum_l G_n[m][l] Im in_l
+// for m < mmax, skipping the chequerboard zeros (Fig. 2).  The packed table
+// pointer advances identically in every lane (warp-uniform loads).
+template <typename T>
+__device__ __forceinline__ void swap_row(const DevTables<T> &tb, int n, LaneArr<T> in_re,
+                                         LaneArr<T> in_im, LaneArr<T> out_re,
+                                         LaneArr<T> out_im, int mmax) {
+    const T *__restrict__ F = tb.F + __ldg(tb.Frow + n);
+    for (int m = 0; m < mmax; ++m) {
+        T acc = T(0);
+#pragma unroll 4
+        for (int l = (n + m) & 1; l <= n; l += 2) acc = fma_t(ldt(F++), in_re[l], acc);
+        out_re[m] = acc;
+    }
+    const T *__restrict__ G = tb.G + __ldg(tb.Grow + n);
+    out_im[0] = T(0);
+    for (int m = 1; m < mmax; ++m) {
+        T acc = T(0);
+#pragma unroll 4
+        for (int l = ((n + m + 1) & 1) ? 1 : 2; l <= n; l += 2) acc = fma_t(ldt(G++), in_im[l], acc);
+        out_im[m] = acc;
+    }
+}
+
+// Output sink: overwrite or add one coefficient of the result.
+template <typename T>
+__device__ __forceinline__ void put(T *dst, T v, bool add) {
+    if (add) v += *dst;
+    *dst = v;
+}
+
+// One translation computed by the calling thread (Sec. 3.4 steps 1-4, with
+// the z-axis translation of the op).  `buf` is this lane's shared memory of
+// lane_elems(p_in, p_out) elements.  add = accumulate into dst.
+template <typename T, int OP>
+__device__ void translate_one(const DevTables<T> &tb, int p_in, int p_out,
+                              const T *__restrict__ src, const T *__restrict__ shift,
+                              T *__restrict__ dst, bool add, LaneArr<T> X, LaneArr<T> buf) {
+    const int P = p_in > p_out ? p_in : p_out;
+    // lane memory map: X = rotated solid (rows k < p_in, p_in(p_in+1) elements),
+    // buf = two row buffers and the powers of e^{i alpha}, e^{i beta} (8P)
+    const int xhalf = p_in * (p_in + 1) / 2;
+    LaneArr<T> Xre = X, Xim = X + xhalf;
+    LaneArr<T> Are = buf, Aim = Are + P;                     // row buffer A
+    LaneArr<T> Bre = Aim + P, Bim = Bre + P;                 // row buffer B
+    LaneArr<T> PAre = Bim + P, PAim = PAre + P;              // e^{i m alpha}
+    LaneArr<T> PBre = PAim + P, PBim = PBre + P;             // e^{i m beta}
+
+    // --- step 1: shift geometry without trigonometric functions (Sec. 3.4)
+    const T x = shift[0], y = shift[1], z = shift[2];
+    const T rho2 = x * x + y * y;
+    const T R = sqrt_t(rho2 + z * z);
+    if (!(R > T(0))) {
+        if (OP != OP_M2L) {
+            // zero shift: M2M / L2L are the identity (truncated or zero-padded)
+            for (int n = 0; n < p_out; ++n)
+                for (int j = 0; j < 2 * (n + 1); ++j)
+                    put(dst + n * (n + 1) + j, n < p_in ? src[n * (n + 1) + j] : T(0), add);
+            return;
+        }
+    }
+    const T rho = sqrt_t(rho2);
+    T ca = T(1), sa = T(0);                     // cos(alpha) = y/rho, sin(alpha) = x/rho
+    if (rho > T(0)) { const T ir = T(1) / rho; ca = y * ir; sa = x * ir; }
+    const T iR = T(1) / R;
+    const T cb = z * iR, sb = -rho * iR;        // cos(beta) = z/|r|, sin(beta) = -rho/|r|
+    {
+        T ar = T(1), ai = T(0), br = T(1), bi = T(0);
+        for (int m = 0; m < P; ++m) {
+            PAre[m] = ar; PAim[m] = ai; PBre[m] = br; PBim[m] = bi;
+            const T ar2 = ar * ca - ai * sa, ai2 = fma_t(ar, sa, ai * ca);
+            const T br2 = br * cb - bi * sb, bi2 = fma_t(br, sb, bi * cb);
+            ar = ar2; ai = ai2; br = br2; bi = bi2;
+        }
+    }
+
+    // --- step 2: rows of the input -> rotated frame, shift along +z, |r| = 1
+    // input scale (eq. scaling): M2L |r|^{-(n+1)}, M2M |r|^{-n}, L2L |r|^{n}
+    const T step_in = (OP == OP_L2L) ? R : iR;
+    T s = (OP == OP_M2L) ? iR : T(1);
+    const int krows = (OP == OP_M2M) ? (p_in < p_out ? p_in : p_out) : p_in;
+    for (int n = 0; n < krows; ++n) {
+        const T *row = src + n * (n + 1);
+        const T *cf = ((OP == OP_L2L) ? tb.ic : tb.c) + n * (n + 1) / 2;
+        // (b) scale, change to the orthonormal basis, rotate by alpha
+        for (int m = 0; m <= n; ++m) {
+            const T f = s * ldt(cf + m);
+            const T re = row[m] * f, im = row[n + 1 + m] * f;
+            const T pr = PAre[m], pi = PAim[m];
+            Are[m] = re * pr - im * pi;
+            Aim[m] = fma_t(re, pi, im * pr);
+        }
+        // (c) swap x and z
+        swap_row(tb, n, Are, Aim, Bre, Bim, n + 1);
+        // (d) rotate by beta
+        for (int m = 1; m <= n; ++m) {
+            const T re = Bre[m], im = Bim[m], pr = PBre[m], pi = PBim[m];
+            Bre[m] = re * pr - im * pi;
+            Bim[m] = fma_t(re, pi, im * pr);
+        }
+        // (e) swap again, straight into the column-ordered rotated solid
+        const int mm = (n + 1 < p_out) ? n + 1 : p_out;
+        const int xo = n * (n + 1) / 2;
+        swap_row(tb, n, Bre, Bim, Xre + xo, Xim + xo, mm);
+        s *= step_in;
+    }
+
+    // --- steps 3-4: per output row, z-axis translation then rotate back
+    // output scale: M2L |r|^{-n}, M2M |r|^{n}, L2L |r|^{-n}
+    const T step_out = (OP == OP_M2M) ? R : iR;
+    T so = T(1);
+    const T *__restrict__ Tz = tb.Tz[OP];
+    const int Pm = tb.Pmax;
+    for (int n = 0; n < p_out; ++n) {
+        for (int m = 0; m <= n; ++m) {
+            const T *Tr = Tz + ztrans_block_offset(Pm, m) + (long long)(n - m) * (Pm - m) - m;
+            int k0 = m, k1 = p_in;                          // M2L: all k >= m
+            if (OP == OP_M2M) k1 = (n + 1 < p_in) ? n + 1 : p_in;
+            if (OP == OP_L2L) k0 = n;
+            T ar = T(0), ai = T(0);
+            int xi = k0 * (k0 + 1) / 2 + m;
+            if (m == 0) {
+                for (int k = k0; k < k1; ++k) { ar = fma_t(ldt(Tr + k), Xre[xi], ar); xi += k + 1; }
+            } else {
+                for (int k = k0; k < k1; ++k) {
+                    const T t = ldt(Tr + k);
+                    ar = fma_t(t, Xre[xi], ar);
+                    ai = fma_t(t, Xim[xi], ai);
+                    xi += k + 1;
+                }
+            }
+            Are[m] = ar; Aim[m] = ai;
+        }
+        // swap, rotate by -beta, swap
+        swap_row(tb, n, Are, Aim, Bre, Bim, n + 1);
+        for (int m = 1; m <= n; ++m) {
+            const T re = Bre[m], im = Bim[m], pr = PBre[m], pi = PBim[m];
+            Bre[m] = fma_t(re, pr, im * pi);
+            Bim[m] = im * pr - re * pi;
+        }
+        swap_row(tb, n, Bre, Bim, Are, Aim, n + 1);
+        // rotate by -alpha, undo the scaling and the basis change, store
+        const T *cf = ((OP == OP_M2M) ? tb.ic : tb.c) + n * (n + 1) / 2;
+        T *orow = dst + n * (n + 1);
+        for (int m = 0; m <= n; ++m) {
+            const T f = so * ldt(cf + m);
+            const T re = Are[m] * f, im = Aim[m] * f;
+            const T pr = PAre[m], pi = PAim[m];
+            put(orow + m, fma_t(re, pr, im * pi), add);
+            put(orow + n + 1 + m, im * pr - re * pi, add);
+        }
+        so *= step_out;
+    }
+}
+
+// ---------------------------------------------------------------- kernels
+
+// Lane storage.  XG = false: everything in shared memory.  XG = true (orders
+// whose rotated solid does not fit): the rotated solid lives in a global
+// scratch area with one slot per resident warp, interleaved like shared
+// memory, and the kernel runs as a persistent grid of exactly `nslots` warps.
+template <typename T, bool XG>
+struct LaneStore {
+    LaneArr<T> X, buf;
+    __device__ __forceinline__ LaneStore(T *smem, T *scratch, int p_in, int p_out) {
+        const int lane = threadIdx.x & (WARP - 1), warp = threadIdx.x / WARP;
+        const int ex = x_elems(p_in), er = row_elems(p_in, p_out);
+        if (XG) {
+            const long long slot = (long long)blockIdx.x * (blockDim.x / WARP) + warp;
+            X = LaneArr<T>{scratch + slot * ex * WARP + lane};
+            buf = LaneArr<T>{smem + (size_t)warp * er * WARP + lane};
+        } else {
+            X = LaneArr<T>{smem + (size_t)warp * (ex + er) * WARP + lane};
+            buf = X + ex;
+        }
+    }
+};
+
+template <typename T, int OP, bool XG>
+__global__ void __launch_bounds__(256) batch_kernel(DevTables<T> tb, const T *const *in,
+                                                    T *const *out, const T *shift, int p_in,
+                                                    int p_out, long long count, int accumulate,
+                                                    T *scratch, int *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LaneStore<T, XG> ls(reinterpret_cast<T *>(smem_raw), scratch, p_in, p_out);
+    const long long stride = XG ? (long long)gridDim.x * blockDim.x : count;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const T *src = in[i];
+        T *dst = out[i];
+        if (src == nullptr || dst == nullptr) { atomicOr(status, STATUS_NULL_POINTER); continue; }
+        translate_one<T, OP>(tb, p_in, p_out, src, shift + 3 * i, dst, accumulate != 0, ls.X, ls.buf);
+    }
+}
+
+template <typename T, int OP, bool XG>
+__global__ void __launch_bounds__(256) lists_kernel(DevTables<T> tb, const T *const *src,
+                                                    const T *shift, const long long *offsets,
+                                                    T *const *out, int p_in, int p_out,
+                                                    long long n_targets, int accumulate,
+                                                    T *scratch, int *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LaneStore<T, XG> ls(reinterpret_cast<T *>(smem_raw), scratch, p_in, p_out);
+    const long long stride = XG ? (long long)gridDim.x * blockDim.x : n_targets;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n_targets; t += stride) {
+        T *dst = out[t];
+        const long long j0 = offsets[t], j1 = offsets[t + 1];
+        if (dst == nullptr) { atomicOr(status, STATUS_NULL_POINTER); continue; }
+        if (j1 < j0) { atomicOr(status, STATUS_BAD_OFFSETS); continue; }
+        bool add = accumulate != 0;
+        if (j0 == j1 && !add)
+            for (int e = 0; e < p_out * (p_out + 1); ++e) dst[e] = T(0);
+        for (long long j = j0; j < j1; ++j) {
+            const T *s = src[j];
+            if (s == nullptr) { atomicOr(status, STATUS_NULL_POINTER); continue; }
+            translate_one<T, OP>(tb, p_in, p_out, s, shift + 3 * j, dst, add, ls.X, ls.buf);
+            add = true;
+        }
+    }
+}
+
+// P2M / P2L for boxes of sorted points: one thread per box, the harmonics of
+// each point by the Appendix recurrences, accumulated in shared memory.
+template <typename T, bool SINGULAR>
+__global__ void __launch_bounds__(128) p2x_kernel(int P, const T *points, const T *q,
+                                                  const long long *offsets, const T *centres,
+                                                  T *out, long long n_boxes, int *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *smem = reinterpret_cast<T *>(smem_raw);
+    const int lane = threadIdx.x & (WARP - 1), warp = threadIdx.x / WARP;
+    const int E = 2 * P * (P + 1);
+    LaneArr<T> H{smem + (size_t)warp * E * WARP + lane};   // harmonics of one point
+    LaneArr<T> A = H + P * (P + 1);                          // accumulator
+    const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_boxes) return;
+    const long long j0 = offsets[b], j1 = offsets[b + 1];
+    if (j1 < j0) { atomicOr(status, STATUS_BAD_OFFSETS); return; }
+    for (int e = 0; e < P * (P + 1); ++e) A[e] = T(0);
+    const T cx = centres[3 * b], cy = centres[3 * b + 1], cz = centres[3 * b + 2];
+    for (long long j = j0; j < j1; ++j) {
+        const T x = points[3 * j] - cx, y = points[3 * j + 1] - cy, z = points[3 * j + 2] - cz;
+        const T r2 = x * x + y * y + z * z;
+        const T ir2 = T(1) / r2;
+        const T qj = q[j];
+        for (int n = 0; n < P; ++n) {
+            const int o = n * (n + 1), o1 = (n - 1) * n, o2 = (n - 2) * (n - 1);
+            for (int m = 0; m <= n; ++m) {
+                T vr, vi;
+                if (n == 0) {
+                    vr = SINGULAR ? T(1) / sqrt_t(r2) : T(1);
+                    vi = T(0);
+                } else if (m == n) {
+                    // diagonal: R_n^n = (x+iy)/(2n) R_{n-1}^{n-1},
+                    //           S_n^n = (2n-1)(x+iy)/|r|^2 S_{n-1}^{n-1}
+                    const T pr = H[o1 + n - 1], pi = H[o1 + n - 1 + n];
+                    const T f = SINGULAR ? T(2 * n - 1) * ir2 : T(1) / T(2 * n);
+                    vr = (x * pr - y * pi) * f;
+                    vi = (x * pi + y * pr) * f;
+                } else {
+                    const T ar = H[o1 + m], ai = H[o1 + n + m];
+                    T br = T(0), bi = T(0);
+                    if (n - 2 >= m) { br = H[o2 + m]; bi = H[o2 + n - 1 + m]; }
+                    if (SINGULAR) {
+                        const T g = T((n - 1) * (n - 1) - m * m);
+                        vr = (T(2 * n - 1) * z * ar - g * br) * ir2;
+                        vi = (T(2 * n - 1) * z * ai - g * bi) * ir2;
+                    } else {
+                        const T g = T(1) / T(n * n - m * m);
+                        vr = (T(2 * n - 1) * z * ar - r2 * br) * g;
+                        vi = (T(2 * n - 1) * z * ai - r2 * bi) * g;
+                    }
+                }
+                H[o + m] = vr;
+                H[o + n + 1 + m] = vi;
+                A[o + m] = fma_t(qj, vr, A[o + m]);
+                A[o + n + 1 + m] = fma_t(qj, vi, A[o + n + 1 + m]);
+            }
+        }
+    }
+    T *dst = out + b * (long long)(P * (P + 1));
+    for (int e = 0; e < P * (P + 1); ++e) dst[e] = A[e];
+}
+
+}  // namespace sfmm

@@ -101,42 +101,35 @@ def _interaction_lists(depth):
     """Standard FMM interaction list at a level: children of the parent's
     neighbours (including the parent itself) that are not adjacent to the
     target box.  Returns CSR arrays in target-major order, sources sorted by
-    box index."""
+    box index within each target."""
     nside, h, ijk, centres = _level_geometry(depth)
     nbox = nside ** 3
     if depth < 2:
         return (np.zeros(nbox + 1, np.int64), np.zeros(0, np.int64),
                 np.zeros((0, 3)), np.zeros(0, np.int64))
     par = ijk // 2
-    offs_all = []
+    tg, sr, cd = [], [], []
     for dx in range(-3, 4):
         for dy in range(-3, 4):
             for dz in range(-3, 4):
-                offs_all.append((dx, dy, dz))
-    offs_all = np.array(offs_all)
-    src_lists = []
-    codes = []
-    counts = np.zeros(nbox, np.int64)
-    for t in range(nbox):
-        s = ijk[t] + offs_all
-        ok = np.all((s >= 0) & (s < nside), axis=1)
-        near = np.all(np.abs(offs_all) <= 1, axis=1)
-        same_par_nb = np.all(np.abs(s // 2 - par[t]) <= 1, axis=1)
-        sel = ok & ~near & same_par_nb
-        sidx = box_index(s[sel, 0], s[sel, 1], s[sel, 2], nside)
-        o = offs_all[sel]
-        code = ((o[:, 0] + 3) * 7 + (o[:, 1] + 3)) * 7 + (o[:, 2] + 3)
-        order = np.argsort(sidx)
-        src_lists.append(sidx[order])
-        codes.append(code[order])
-        counts[t] = len(sidx)
+                if max(abs(dx), abs(dy), abs(dz)) <= 1:
+                    continue                    # adjacent boxes are near field
+                o = np.array([dx, dy, dz])
+                s = ijk + o
+                ok = np.all((s >= 0) & (s < nside), axis=1)
+                ok &= np.all(np.abs(s // 2 - par) <= 1, axis=1)
+                t = np.nonzero(ok)[0]
+                tg.append(t)
+                sr.append(box_index(s[t, 0], s[t, 1], s[t, 2], nside))
+                cd.append(np.full(len(t), ((dx + 3) * 7 + (dy + 3)) * 7 + (dz + 3)))
+    tg, sr, cd = np.concatenate(tg), np.concatenate(sr), np.concatenate(cd)
+    order = np.lexsort((sr, tg))
+    tg, sr, cd = tg[order], sr[order], cd[order]
+    counts = np.bincount(tg, minlength=nbox)
     offsets = np.zeros(nbox + 1, np.int64)
     np.cumsum(counts, out=offsets[1:])
-    sources = np.concatenate(src_lists).astype(np.int64)
-    code = np.concatenate(codes).astype(np.int64)
-    tgt = np.repeat(np.arange(nbox), counts)
-    shift = centres[tgt] - centres[sources]
-    return offsets, sources, shift, code
+    shift = centres[tg] - centres[sr]
+    return offsets, sr.astype(np.int64), shift, cd.astype(np.int64)
 
 
 def uniform_octree(depth, npoints=0, seed=2):

@@ -1,0 +1,246 @@
+"""CUDA path against the oracle, element by element, through the C ABI.
+
+Tolerances: the weighted relative coefficient error (tests/gpu_util.py) must
+be <= 1e-12 in FP64 and <= 1e-5 in FP32 (FP32 at P <= 10)."""
+import numpy as np
+import pytest
+
+from paper_2202_02847_gb300 import workloads as W
+import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def sf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_2202_02847_gb300 import sfmm
+    return sfmm
+
+
+@pytest.fixture(scope="module")
+def h64(sf):
+    h = sf.Handle(32, "f64")
+    yield h
+    h.close()
+
+
+@pytest.fixture(scope="module")
+def h32(sf):
+    h = sf.Handle(16, "f32")
+    yield h
+    h.close()
+
+
+def _config1_inputs(orc, sf, count, P, seed, op):
+    """32 charges uniform in a unit box at the origin, q ~ U[-1,1]; multipoles
+    by P2M about the origin, locals by P2L about a centre at distance 3.
+    Each side forms its own expansions from the same charges."""
+    import torch
+    g = W.rng(seed)
+    pos, q = W.charge_clusters(g, count, 32)
+    sh = W.shifts(g, count, 2.0, 4.0)
+    far = W.unit_directions(g, count) * 3.0
+    centres = np.zeros((count, 3)) if op != "l2l" else far
+    C = np.stack([(orc.p2m if op != "l2l" else orc.p2l)(P, pos[i], q[i], centres[i])
+                  for i in range(count)])
+    # the same expansions formed on the device by the library's own P2M / P2L
+    h = sf.Handle(P, "f64")
+    dev = "cuda"
+    pts = torch.tensor(pos.reshape(-1, 3), device=dev)
+    qq = torch.tensor(q.reshape(-1), device=dev)
+    offs = torch.arange(0, 32 * count + 1, 32, dtype=torch.int64, device=dev)
+    cen = torch.tensor(centres, device=dev)
+    out = torch.zeros(count, P * (P + 1), dtype=torch.float64, device=dev)
+    (sf.p2m_boxes if op != "l2l" else sf.p2l_boxes)(h, P, pts, qq, offs, cen, out, count)
+    torch.cuda.synchronize()
+    Cg = out.cpu().numpy()
+    h.close()
+    return C, Cg, sh
+
+
+@pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
+def test_config1_p6_4096(sf, orc, h64, op):
+    """plain FP64, P = 6: 4096 translations of each kind from P2M/P2L of 32
+    charges, shift = random unit direction x U[2,4]."""
+    P, count = 6, 4096
+    C, Cg, sh = _config1_inputs(orc, sf, count, P, 1, op)
+    kind_in = "L" if op == "l2l" else "M"
+    assert U.rel_err(Cg, C, P, kind_in) < 1e-14          # device P2M / P2L
+    got = U.run_batch(sf, h64, op, Cg, sh, P, P, "f64")
+    want, _ = orc.batch(op, P, P, C, sh)
+    err = U.rel_err(got, want, P, U.out_kind(op))
+    assert err <= TOL["f64"], err
+
+
+@pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
+@pytest.mark.parametrize("p_in,p_out", [(1, 1), (1, 4), (4, 1), (2, 2), (5, 8), (8, 5),
+                                        (10, 10), (13, 7)])
+def test_mixed_orders(sf, orc, h64, op, p_in, p_out):
+    g = W.rng(1000 + 17 * p_in + p_out)
+    count = 77
+    C = W.random_solids(g, count, p_in)
+    sh = W.shifts(g, count, 2.0, 4.0)
+    got = U.run_batch(sf, h64, op, C, sh, p_in, p_out, "f64")
+    want, _ = orc.batch(op, p_in, p_out, C, sh)
+    assert U.rel_err(got, want, p_out, U.out_kind(op)) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
+@pytest.mark.parametrize("P", [16, 20, 27, 32])
+def test_high_orders(sf, orc, h64, op, P):
+    g = W.rng(2000 + P)
+    count = 40
+    C = W.random_solids(g, count, P, decay=0.4)
+    sh = W.shifts(g, count, 2.0, 4.0)
+    got = U.run_batch(sf, h64, op, C, sh, P, P, "f64")
+    want, _ = orc.batch(op, P, P, C, sh)
+    assert U.rel_err(got, want, P, U.out_kind(op)) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("count", [1, 31, 33, 257])
+def test_ragged_counts(sf, orc, h64, count):
+    g = W.rng(3000 + count)
+    P = 7
+    C = W.random_solids(g, count, P)
+    sh = W.shifts(g, count)
+    got = U.run_batch(sf, h64, "m2l", C, sh, P, P, "f64")
+    want, _ = orc.batch("m2l", P, P, C, sh)
+    assert U.rel_err(got, want, P, "L") <= TOL["f64"]
+
+
+def test_count_zero_is_noop(sf, h64):
+    sf.m2l_batch(h64, 0, 0, 0, 4, 4, 0)
+
+
+@pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
+def test_special_shifts(sf, orc, h64, op):
+    """Shifts along +z and -z (rho = 0, cos(alpha) = 1 by the special case of
+    Sec. 3.4 step 1), nearly axial shifts, and axis-aligned shifts."""
+    P = 9
+    sh = np.array([[0, 0, 3.0], [0, 0, -2.5], [1e-170, 0, 3.0], [0, 1e-9, -2.2],
+                   [3.0, 0, 0], [0, -2.4, 0], [2.0, 2.0, 0], [-1.5, 0, 1.5]])
+    g = W.rng(4000)
+    C = W.random_solids(g, len(sh), P)
+    got = U.run_batch(sf, h64, op, C, sh, P, P, "f64")
+    want, _ = orc.batch(op, P, P, C, sh)
+    assert U.rel_err(got, want, P, U.out_kind(op)) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("op", ["m2m", "l2l"])
+def test_zero_shift_is_identity(sf, h64, op):
+    P = 6
+    g = W.rng(4100)
+    C = W.random_solids(g, 5, P)
+    got = U.run_batch(sf, h64, op, C, np.zeros((5, 3)), P, P, "f64")
+    assert np.array_equal(got, C)
+    got = U.run_batch(sf, h64, op, C, np.zeros((5, 3)), P, P + 2, "f64")
+    assert np.array_equal(got[:, :P * (P + 1)], C) and not got[:, P * (P + 1):].any()
+
+
+@pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
+def test_accumulate(sf, orc, h64, op):
+    P = 8
+    g = W.rng(4200)
+    C = W.random_solids(g, 50, P)
+    sh = W.shifts(g, 50)
+    init = W.random_solids(g, 50, P)
+    got = U.run_batch(sf, h64, op, C, sh, P, P, "f64", accumulate=True, init=init)
+    want, _ = orc.batch(op, P, P, C, sh)
+    assert U.rel_err(got - init, want, P, U.out_kind(op)) <= 1e-11
+
+
+def test_result_independent_of_batch(sf, h64):
+    """Each translation gives bitwise the same result alone and inside a mix."""
+    P = 8
+    g = W.rng(4300)
+    C = W.random_solids(g, 300, P)
+    sh = W.shifts(g, 300)
+    full = U.run_batch(sf, h64, "m2l", C, sh, P, P, "f64")
+    for i in (0, 123, 299):
+        one = U.run_batch(sf, h64, "m2l", C[i:i + 1], sh[i:i + 1], P, P, "f64")
+        assert np.array_equal(one[0], full[i])
+
+
+@pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
+@pytest.mark.parametrize("P", [6, 10])
+def test_fp32(sf, orc, h32, op, P):
+    g = W.rng(5000 + P)
+    count = 200
+    C = W.random_solids(g, count, P)
+    sh = W.shifts(g, count)
+    got = U.run_batch(sf, h32, op, C.astype(np.float32), sh.astype(np.float32), P, P, "f32")
+    # the oracle sees exactly the FP32-rounded inputs
+    want, _ = orc.batch(op, P, P, C.astype(np.float32).astype(np.float64),
+                        sh.astype(np.float32).astype(np.float64))
+    assert U.rel_err(got, want, P, U.out_kind(op)) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_lists(sf, orc, h64, op, accumulate):
+    """Target-major CSR lists with lengths 0..40 (sum in list order)."""
+    import torch
+    P_in, P_out = 7, 6
+    g = W.rng(6000 + accumulate)
+    nt = 70
+    lens = g.integers(0, 41, size=nt)
+    lens[3] = 0
+    offs = np.zeros(nt + 1, np.int64)
+    np.cumsum(lens, out=offs[1:])
+    nnz = int(offs[-1])
+    nsrc = 90
+    S = W.random_solids(g, nsrc, P_in)
+    src_idx = g.integers(0, nsrc, size=nnz)
+    sh = W.shifts(g, nnz)
+    init = W.random_solids(g, nt, P_out)
+    dev = "cuda"
+    dS = torch.tensor(S, device=dev)
+    dO = torch.tensor(init, device=dev)
+    psrc = sf.pointer_array(dS, P_in * (P_in + 1), torch.tensor(src_idx))
+    pout = sf.pointer_array(dO, P_out * (P_out + 1), torch.arange(nt))
+    sf.translate_lists(h64, op, psrc, torch.tensor(sh, device=dev),
+                       torch.tensor(offs, device=dev), pout, P_in, P_out, nt,
+                       accumulate=accumulate)
+    torch.cuda.synchronize()
+    assert h64.sync_status() == 0
+    got = dO.cpu().numpy()
+    each, _ = orc.batch(op, P_in, P_out, S[src_idx], sh)
+    want = init.copy() if accumulate else np.zeros_like(init)
+    for t in range(nt):
+        for j in range(offs[t], offs[t + 1]):
+            want[t] += each[j]
+    assert U.rel_err(got, want, P_out, U.out_kind(op)) <= TOL["f64"]
+
+
+def test_device_status_reports_null_pointer(sf, h64):
+    import torch
+    P = 4
+    cin = torch.zeros(2, P * (P + 1), dtype=torch.float64, device="cuda")
+    cout = torch.zeros_like(cin)
+    pin = sf.pointer_array(cin, P * (P + 1), torch.arange(2))
+    pin[1] = 0
+    pout = sf.pointer_array(cout, P * (P + 1), torch.arange(2))
+    shift = torch.ones(2, 3, dtype=torch.float64, device="cuda")
+    sf.m2l_batch(h64, pin, pout, shift, P, P, 2)
+    torch.cuda.synchronize()
+    assert h64.sync_status() == 1
+    assert h64.sync_status() == 0          # cleared by the read
+
+
+def test_host_errors(sf, h64):
+    with pytest.raises(sf.SfmmError) as e:
+        sf.m2l_batch(h64, 1, 1, 1, 0, 4, 1)
+    assert e.value.code == 2
+    with pytest.raises(sf.SfmmError) as e:
+        sf.m2l_batch(h64, 1, 1, 1, 4, 33, 1)
+    assert e.value.code == 2
+    with pytest.raises(sf.SfmmError) as e:
+        sf.m2l_batch(h64, 0, 0, 0, 4, 4, 5)
+    assert e.value.code == 1
