@@ -1,0 +1,402 @@
+"""Benchmark: M2L translations/s of the FP64 uniform-octree translation pass.
+
+Workload (plain FP64, P = 10): uniform octree of depth 5 (32^3 leaves) over
+1,048,576 points uniform in the unit cube with q ~ U[-1,1] (seed 2, or 2+rank
+per GPU).  One step = the whole translation pass on the device: M2M from the
+leaves to the root (37,448 translations), every M2L of the interaction lists
+of levels 2..5 (6,039,504 translations, in one launch) and L2L from level 2 to
+the leaves (37,376).  value = M2L translations of all ranks / (max over ranks
+of the time of K steps); the M2M and L2L time is included in the denominator.
+
+Also reported: the roofline of the dominant kernel (the M2L launch), the
+end-to-end rate with the leaf multipoles copied in and the leaf locals copied
+out every step, the oracle's rate on the host cores on a bounded sample of
+the same M2L list, and the weighted relative error against the oracle on a
+sampled set of targets.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "M2L translations/s vs order P at stated rel. error; serving p50/p99 latency"
+UNIT = "translations/s"
+DEPTH, P, NPOINTS, SEED = 5, 10, 1 << 20, 2
+# GB300 FP64 pipe: 2 FMA/clk/SM (measured with a DFMA loop at >= 4 warps/SM,
+# matching the nominal 1.25 TFLOP/s) x 152 SMs x 2 FLOP x max SM clock.
+FP64_FMA_PER_CLK_SM = 2
+L2_FLUSH_BYTES = 512 << 20
+
+
+def m2l_flop(p):
+    """Algorithmic FLOP of one rotation-based M2L of order p: the O(p^3)
+    swaps and z-translation, 2p(p+1)(2p+1), plus 14p(p+1) for scaling and
+    z-rotations."""
+    return 2 * p * (p + 1) * (2 * p + 1) + 14 * p * (p + 1)
+
+
+def m2l_bytes(p, w=8):
+    """Algorithmic bytes of one M2L: solid in and out, shift, two pointers."""
+    return w * (2 * p * (p + 1)) + 3 * w + 16
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2202_02847_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".cpp", ".h")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per M2L launch from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "m2l_lists_fp64_p10_octree_l5.md")
+    if not os.path.exists(path):
+        return None
+    kh, tr = None, None
+    for line in open(path):
+        if line.startswith("kernel_sources_sha256_16:"):
+            kh = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            tr = float(line.split(":", 1)[1].strip())
+    return tr if kh == kernel_hash() else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.lines = index, None, []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n):
+    import torch
+    import torch.distributed as dist
+    if n > 1 or "RANK" in os.environ:
+        rank = int(os.environ.get("RANK", 0))
+        local = int(os.environ.get("LOCAL_RANK", 0))
+        world = int(os.environ.get("WORLD_SIZE", 1))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        return rank, local, world, dist
+    return 0, 0, 1, None
+
+
+def sample_targets(fp, k, seed):
+    """k level-5 targets (seeded) of the M2L plan, with their CSR slice."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    lvl_lo = int(fp.level_base[DEPTH])
+    cand = np.nonzero(fp.m2l_targets >= lvl_lo)[0]
+    pick = np.sort(g.choice(cand, size=k, replace=False))
+    return pick
+
+
+def oracle_parity_and_rate(fp, tree, dev_result, picks, budget_s):
+    """The oracle leg: (a) the oracle's M2L rate on the host cores over a
+    bounded prefix of the level-5 M2L list, (b) the weighted relative error of
+    the device's M2L results for the sampled targets against the oracle.  The
+    oracle forms its own leaf multipoles from the particles."""
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import gpu_util as U
+    o = oracle.get()
+    S = P * (P + 1)
+    lvl_lo = int(fp.level_base[DEPTH])
+    pts, q, leaf = tree.points, tree.charges, tree.leaf_of_point
+    order = np.argsort(leaf, kind="stable")
+    counts = np.bincount(leaf, minlength=8 ** DEPTH)
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    centres = tree.levels[DEPTH].centres
+    cache = {}
+
+    def M_of(box):
+        if box not in cache:
+            sel = order[offs[box]:offs[box + 1]]
+            cache[box] = o.p2m(P, pts[sel], q[sel], centres[box])
+        return cache[box]
+
+    # (b) parity on sampled targets
+    worst = 0.0
+    got_all, want_all = [], []
+    for t in picks:
+        j0, j1 = fp.m2l_offsets_host[t], fp.m2l_offsets_host[t + 1]
+        srcs = fp.m2l_src_host[j0:j1] - lvl_lo
+        Ms = np.stack([M_of(int(b)) for b in srcs])
+        each, _ = o.batch("m2l", P, P, Ms, fp.m2l_shift_host[j0:j1])
+        want_all.append(each.sum(axis=0))
+        got_all.append(dev_result[t])
+    err = U.rel_err(np.array(got_all), np.array(want_all), P, "L")
+    # (c) rate: bounded prefix of the level-5 list, all host cores
+    nthreads = os.cpu_count() or 1
+    j = 0
+    done = 0
+    t_used = 0.0
+    chunk = 20000
+    src5 = np.nonzero(fp.m2l_src_host >= lvl_lo)[0]
+    while t_used < budget_s and j < len(src5):
+        sel = src5[j:j + chunk]
+        Ms = np.stack([M_of(int(b) - lvl_lo) for b in fp.m2l_src_host[sel]])
+        t0 = time.perf_counter()
+        _, used = o.batch("m2l", P, P, Ms, fp.m2l_shift_host[sel], nthreads=nthreads)
+        t_used += time.perf_counter() - t0
+        done += len(sel)
+        j += chunk
+    return err, done / t_used, done, used
+
+
+def run_reference(args):
+    """--impl reference: the oracle as it stands on the host cores, on
+    bounded samples of the same M2L workload."""
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2202_02847_gb300 import workloads as W
+    o = oracle.get()
+    tree = W.uniform_octree(DEPTH, NPOINTS, seed=SEED)
+    lv = tree.levels[DEPTH]
+    per_step = 4000
+    g = W.rng(7)
+    # inputs: the oracle's own multipoles of the sampled source leaves
+    order = np.argsort(tree.leaf_of_point, kind="stable")
+    counts = np.bincount(tree.leaf_of_point, minlength=8 ** DEPTH)
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    idx = g.choice(len(lv.m2l_sources), size=per_step, replace=False)
+    Ms = []
+    for b in lv.m2l_sources[idx]:
+        sel = order[offs[b]:offs[b + 1]]
+        Ms.append(o.p2m(P, tree.points[sel], tree.charges[sel], lv.centres[b]))
+    Ms = np.stack(Ms)
+    sh = lv.m2l_shift[idx]
+    nthreads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        o.batch("m2l", P, P, Ms, sh, nthreads=nthreads)
+    t0 = time.perf_counter()
+    used = 1
+    for _ in range(args.steps):
+        _, used = o.batch("m2l", P, P, Ms, sh, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "plain FP64 P=10 uniform octree level 5 M2L list (oracle, "
+                               "sample of 4000 translations per step)", "P": P},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                         "sample": f"{per_step} seeded translations of the level-5 M2L list per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sfmm", choices=["sfmm", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0,
+                    help="seconds of oracle work for the cpu_baseline leg")
+    ap.add_argument("--no-oracle", action="store_true")
+    ap.add_argument("--depth", type=int, default=DEPTH,
+                    help="octree depth (5 = the benchmark workload; smaller for profiling)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import __graft_entry__
+    rank, local, world, dist = dist_setup(args.gpus)
+    if rank == 0:
+        __graft_entry__.build_library()
+    if dist is not None:
+        dist.barrier()
+    from paper_2202_02847_gb300 import multirank, sfmm, workloads as W
+    from paper_2202_02847_gb300.fmm import UniformPass
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    depth = args.depth
+    tree = W.uniform_octree(depth, NPOINTS, seed=multirank.rank_seed(SEED, rank))
+    h = sfmm.Handle(P, "f64")
+    fp = UniformPass(tree, P, h, device=dev)
+    fp.p2m_leaves(tree.points, tree.charges, tree.leaf_of_point)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        fp.step()
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))             # evict the previous step from L2
+            e = ev[k]
+            e[0].record(stream)
+            fp.upward()
+            e[1].record(stream)
+            fp.m2l_all()
+            e[2].record(stream)
+            fp.downward()
+            e[3].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    m2l_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    m2l_per_step = fp.counts["m2l"]
+    value, tmax = multirank.aggregate_rate(m2l_per_step * args.steps, float(sum(step_ms)) * 1e-3, dev)
+    total_ms = tmax * 1e3
+    if dist is not None:
+        dist.barrier()
+    assert h.sync_status() == 0
+
+    # ---- end to end: leaf multipoles in from pinned host memory, leaf locals out
+    leafM = fp.leaf_slice("M")
+    leafL = fp.leaf_slice("L")
+    hM = torch.empty(leafM.shape, dtype=leafM.dtype, pin_memory=True)
+    hM.copy_(leafM)
+    hL = torch.empty(leafL.shape, dtype=leafL.dtype, pin_memory=True)
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(e2e_steps):
+        leafM.copy_(hM, non_blocking=True)
+        fp.step()
+        hL.copy_(leafL, non_blocking=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value, _ = multirank.aggregate_rate(m2l_per_step * e2e_steps, t0.elapsed_time(t1) * 1e-3, dev)
+
+    # ---- roofline of the M2L launch
+    m2l_mean_s = float(np.mean(m2l_ms)) * 1e-3
+    flop = m2l_flop(P) * m2l_per_step
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    sm_max = 2070.0
+    if os.path.exists(peaks_path):
+        sm_max = float(json.load(open(peaks_path)).get("sm_max_mhz", sm_max))
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = nsm * FP64_FMA_PER_CLK_SM * 2 * sm_max * 1e6
+    roof = {"bound": "alu", "achieved": flop / m2l_mean_s / 1e12, "peak": peak / 1e12,
+            "unit": "TFLOP/s", "frac": flop / m2l_mean_s / peak,
+            "traffic": ncu_traffic(), "kernel": "lists_kernel<double, M2L> (one launch per step)",
+            "m2l_ms_mean": m2l_mean_s * 1e3,
+            "hbm_gbs_algorithmic": m2l_bytes(P) * m2l_per_step / m2l_mean_s / 1e9}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"plain FP64 P=10: uniform octree level {depth} "
+                               f"({2 ** depth}^3 leaves), 1M uniform points, full M2M/M2L/L2L "
+                               "translation pass",
+                   "P": P, "depth": depth, "points_per_rank": NPOINTS,
+                   "m2l_per_step": m2l_per_step, "m2m_per_step": fp.counts["m2m"],
+                   "l2l_per_step": fp.counts["l2l"], "l2_flush": True,
+                   "parallelism": f"{world} independent octrees (one per GPU)"},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(leafM.numel() * leafM.element_size()),
+                "d2h_bytes_per_step": int(leafL.numel() * leafL.element_size())},
+        "gpu_launches": fp.launches_per_step() * args.steps,
+    }
+    clocks = clk.summary()
+    if clocks:
+        line["clocks"] = clocks
+
+    if rank == 0 and not args.no_oracle and depth == DEPTH:
+        # device M2L result for sampled targets (M2L only, into a scratch copy)
+        picks = sample_targets(fp, 24, 11)
+        torch.cuda.synchronize()
+        fp.m2l_all()
+        torch.cuda.synchronize()
+        Lhost = fp.L.cpu().numpy()
+        dev_res = Lhost[fp.m2l_targets]
+        err, rate, done, used = oracle_parity_and_rate(fp, tree, dev_res, picks, args.cpu_budget)
+        line["rel_err_vs_oracle"] = {"weighted": err, "targets": len(picks),
+                                     "translations": int(sum(fp.m2l_offsets_host[t + 1] - fp.m2l_offsets_host[t] for t in picks))}
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
+                                "sample": f"first {done} translations of the level-5 M2L list "
+                                          f"(about {args.cpu_budget:.0f} s of oracle work)"}
+    if rank == 0:
+        print(json.dumps(line))
+    h.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

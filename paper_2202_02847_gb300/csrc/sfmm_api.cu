@@ -164,24 +164,40 @@ struct ScratchGuard {
     }
 };
 
-template <typename T, int OP>
-void batch_launch(const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
-                  const T *const *I, T *const *O, const T *S, int p_in, int p_out,
-                  long long count, int acc, T *scratch, int *status) {
-    if (g.xg)
-        batch_kernel<T, OP, true><<<(unsigned)g.blocks, g.warps * WARP, g.smem, stream>>>(tb, I, O, S, p_in, p_out, count, acc, scratch, status);
-    else
-        batch_kernel<T, OP, false><<<(unsigned)g.blocks, g.warps * WARP, g.smem, stream>>>(tb, I, O, S, p_in, p_out, count, acc, scratch, status);
+// Persistent grid: no more blocks than the device holds at once.
+template <typename K>
+long long resident_blocks(const sfmm_ctx *h, K kernel, const Geometry &g) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, g.warps * WARP, g.smem) != cudaSuccess || nb < 1)
+        nb = 1;
+    long long cap = (long long)nb * h->sm_count;
+    return g.blocks < cap ? g.blocks : cap;
 }
 
 template <typename T, int OP>
-void lists_launch(const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
+void batch_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
+                  const T *const *I, T *const *O, const T *S, int p_in, int p_out,
+                  long long count, int acc, T *scratch, int *status) {
+    if (g.xg) {
+        auto k = batch_kernel<T, OP, true>;
+        k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, I, O, S, p_in, p_out, count, acc, scratch, status);
+    } else {
+        auto k = batch_kernel<T, OP, false>;
+        k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, I, O, S, p_in, p_out, count, acc, scratch, status);
+    }
+}
+
+template <typename T, int OP>
+void lists_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
                   const T *const *Sp, const T *S, const long long *offsets, T *const *O,
                   int p_in, int p_out, long long nt, int acc, T *scratch, int *status) {
-    if (g.xg)
-        lists_kernel<T, OP, true><<<(unsigned)g.blocks, g.warps * WARP, g.smem, stream>>>(tb, Sp, S, offsets, O, p_in, p_out, nt, acc, scratch, status);
-    else
-        lists_kernel<T, OP, false><<<(unsigned)g.blocks, g.warps * WARP, g.smem, stream>>>(tb, Sp, S, offsets, O, p_in, p_out, nt, acc, scratch, status);
+    if (g.xg) {
+        auto k = lists_kernel<T, OP, true>;
+        k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, Sp, S, offsets, O, p_in, p_out, nt, acc, scratch, status);
+    } else {
+        auto k = lists_kernel<T, OP, false>;
+        k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, Sp, S, offsets, O, p_in, p_out, nt, acc, scratch, status);
+    }
 }
 
 template <typename T>
@@ -196,9 +212,9 @@ sfmm_status launch_batch(sfmm_handle h, int op, const void *const *in, void *con
     auto S = reinterpret_cast<const T *>(shift);
     T *scr = reinterpret_cast<T *>(h->d_scratch);
     ScratchGuard guard(h, stream, g.xg);
-    if (op == OP_M2M) batch_launch<T, OP_M2M>(g, stream, tb, I, O, S, p_in, p_out, count, accumulate, scr, h->d_status);
-    else if (op == OP_M2L) batch_launch<T, OP_M2L>(g, stream, tb, I, O, S, p_in, p_out, count, accumulate, scr, h->d_status);
-    else batch_launch<T, OP_L2L>(g, stream, tb, I, O, S, p_in, p_out, count, accumulate, scr, h->d_status);
+    if (op == OP_M2M) batch_launch<T, OP_M2M>(h, g, stream, tb, I, O, S, p_in, p_out, count, accumulate, scr, h->d_status);
+    else if (op == OP_M2L) batch_launch<T, OP_M2L>(h, g, stream, tb, I, O, S, p_in, p_out, count, accumulate, scr, h->d_status);
+    else batch_launch<T, OP_L2L>(h, g, stream, tb, I, O, S, p_in, p_out, count, accumulate, scr, h->d_status);
     return cudaGetLastError() == cudaSuccess ? SFMM_OK : SFMM_ERR_CUDA;
 }
 
@@ -215,9 +231,9 @@ sfmm_status launch_lists(sfmm_handle h, int op, const void *const *src, const vo
     auto S = reinterpret_cast<const T *>(shift);
     T *scr = reinterpret_cast<T *>(h->d_scratch);
     ScratchGuard guard(h, stream, g.xg);
-    if (op == OP_M2M) lists_launch<T, OP_M2M>(g, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, scr, h->d_status);
-    else if (op == OP_M2L) lists_launch<T, OP_M2L>(g, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, scr, h->d_status);
-    else lists_launch<T, OP_L2L>(g, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, scr, h->d_status);
+    if (op == OP_M2M) lists_launch<T, OP_M2M>(h, g, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, scr, h->d_status);
+    else if (op == OP_M2L) lists_launch<T, OP_M2L>(h, g, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, scr, h->d_status);
+    else lists_launch<T, OP_L2L>(h, g, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, scr, h->d_status);
     return cudaGetLastError() == cudaSuccess ? SFMM_OK : SFMM_ERR_CUDA;
 }
 

@@ -55,29 +55,110 @@ struct LaneArr {
     __device__ __forceinline__ LaneArr operator+(int e) const { return LaneArr{p + e * WARP}; }
 };
 
+// G outputs of one parity class of a swap: out[m + 2j] = sum_l t_j[i] in[l],
+// l = l0, l0+2, ..., <= n, where t_j = t + j*tstep is the packed table row of
+// output m + 2j.  Outputs of one class share the same l (chequerboard,
+// Fig. 2), so each input is loaded once for G independent FMA chains.
+template <typename T, int G>
+__device__ __forceinline__ void swap_group(const T *__restrict__ t, int tstep, int l0, int n,
+                                           LaneArr<T> in, LaneArr<T> out, int m) {
+    T acc[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) acc[j] = T(0);
+    int i = 0;
+#pragma unroll 2
+    for (int l = l0; l <= n; l += 2, ++i) {
+        const T x = in[l];
+#pragma unroll
+        for (int j = 0; j < G; ++j) acc[j] = fma_t(ldt(t + j * tstep + i), x, acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < G; ++j) out[m + 2 * j] = acc[j];
+}
+
+// All outputs m = m_first, m_first+2, ... < mmax of one parity class, in
+// groups of 4, 2, 1.  off0 = packed offset of output m_first; consecutive
+// outputs of the class are tstep entries apart.
+template <typename T>
+__device__ __forceinline__ void swap_class(const T *__restrict__ t, int off0, int tstep, int l0,
+                                           int n, LaneArr<T> in, LaneArr<T> out, int m_first,
+                                           int mmax) {
+    int m = m_first, off = off0;
+    for (; m + 6 < mmax; m += 8, off += 4 * tstep) swap_group<T, 4>(t + off, tstep, l0, n, in, out, m);
+    if (m + 2 < mmax) { swap_group<T, 2>(t + off, tstep, l0, n, in, out, m); m += 4; off += 2 * tstep; }
+    if (m < mmax) swap_group<T, 1>(t + off, tstep, l0, n, in, out, m);
+}
+
 // One axis swap of row n (eq. Mswapxz / FGmappings):
 //   Re out_m = sum_l F_n[m][l] Re in_l,   Im out_m = sum_l G_n[m][l] Im in_l
-// for m < mmax, skipping the chequerboard zeros (Fig. 2).  The packed table
-// pointer advances identically in every lane (warp-uniform loads).
+// for m < mmax, skipping the chequerboard zeros (Fig. 2).  F_n[m] has its
+// non-zeros at l = (n+m)&1, +2, ...; G_n[m] (m >= 1) at l = 1 or 2, +2, ...
+// with n+m+l odd.  The packed tables hold the rows one after the other, so
+// rows of one parity class are a constant stride apart.
 template <typename T>
 __device__ __forceinline__ void swap_row(const DevTables<T> &tb, int n, LaneArr<T> in_re,
                                          LaneArr<T> in_im, LaneArr<T> out_re,
                                          LaneArr<T> out_im, int mmax) {
     const T *__restrict__ F = tb.F + __ldg(tb.Frow + n);
-    for (int m = 0; m < mmax; ++m) {
-        T acc = T(0);
-#pragma unroll 4
-        for (int l = (n + m) & 1; l <= n; l += 2) acc = fma_t(ldt(F++), in_re[l], acc);
-        out_re[m] = acc;
-    }
+    const int fe = n / 2 + 1;                  // entries of a row with n+m even (l0 = 0)
+    const int fo = (n + 1) / 2;                // entries of a row with n+m odd (l0 = 1)
+    const int f0 = (n & 1) ? fo : fe;          // row m = 0
+    swap_class(F, 0, fe + fo, n & 1, n, in_re, out_re, 0, mmax);
+    swap_class(F, f0, fe + fo, (n + 1) & 1, n, in_re, out_re, 1, mmax);
     const T *__restrict__ G = tb.G + __ldg(tb.Grow + n);
+    const int ge = (n + 1) / 2;                // rows with n+m even: l0 = 1
+    const int go = n / 2;                      // rows with n+m odd:  l0 = 2
+    const int g1 = ((n + 1) & 1) ? go : ge;    // row m = 1
     out_im[0] = T(0);
-    for (int m = 1; m < mmax; ++m) {
-        T acc = T(0);
-#pragma unroll 4
-        for (int l = ((n + m + 1) & 1) ? 1 : 2; l <= n; l += 2) acc = fma_t(ldt(G++), in_im[l], acc);
-        out_im[m] = acc;
+    swap_class(G, 0, ge + go, ((n + 1) & 1) ? 2 : 1, n, in_im, out_im, 1, mmax);
+    swap_class(G, g1, ge + go, (n & 1) ? 2 : 1, n, in_im, out_im, 2, mmax);
+}
+
+// z-axis translation of output row n, columns m0 .. m0+G-1 (eq. zm2lkernels
+// for M2L): out_m = sum_k Tz_m[n][k] X[k][m] for the op's range of k, real
+// and imaginary parts (which do not couple) as 2G independent FMA chains.
+template <typename T, int OP, int G>
+__device__ __forceinline__ void ztrans_block(const T *__restrict__ Tz, int Pm, int n, int m0,
+                                             int p_in, LaneArr<T> Xre, LaneArr<T> Xim,
+                                             LaneArr<T> Are, LaneArr<T> Aim) {
+    const T *Tr[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        const int m = m0 + j;
+        Tr[j] = Tz + ztrans_block_offset(Pm, m) + (long long)(n - m) * (Pm - m) - m;
     }
+    // k ranges: M2L [m, p_in), M2M [m, min(n+1, p_in)), L2L [n, p_in)
+    const int k1 = (OP == OP_M2M) ? ((n + 1 < p_in) ? n + 1 : p_in) : p_in;
+    const int kfull = (OP == OP_L2L) ? n : m0 + G - 1;     // every column active from here
+    int k = (OP == OP_L2L) ? n : m0;
+    T ar[G], ai[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) { ar[j] = T(0); ai[j] = T(0); }
+    const bool has_im0 = m0 > 0;                            // Im of column 0 is zero
+    // head: columns start one after the other (M2L, M2M)
+    for (; k < kfull && k < k1; ++k) {
+        const int xi = k * (k + 1) / 2 + m0;
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (m0 + j <= k) {
+                const T t = ldt(Tr[j] + k);
+                ar[j] = fma_t(t, Xre[xi + j], ar[j]);
+                if (j > 0 || has_im0) ai[j] = fma_t(t, Xim[xi + j], ai[j]);
+            }
+        }
+    }
+#pragma unroll 2
+    for (; k < k1; ++k) {
+        const int xi = k * (k + 1) / 2 + m0;
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            const T t = ldt(Tr[j] + k);
+            ar[j] = fma_t(t, Xre[xi + j], ar[j]);
+            if (j > 0 || has_im0) ai[j] = fma_t(t, Xim[xi + j], ai[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < G; ++j) { Are[m0 + j] = ar[j]; Aim[m0 + j] = ai[j]; }
 }
 
 // Output sink: overwrite or add one coefficient of the result.
@@ -170,25 +251,10 @@ __device__ void translate_one(const DevTables<T> &tb, int p_in, int p_out,
     const T *__restrict__ Tz = tb.Tz[OP];
     const int Pm = tb.Pmax;
     for (int n = 0; n < p_out; ++n) {
-        for (int m = 0; m <= n; ++m) {
-            const T *Tr = Tz + ztrans_block_offset(Pm, m) + (long long)(n - m) * (Pm - m) - m;
-            int k0 = m, k1 = p_in;                          // M2L: all k >= m
-            if (OP == OP_M2M) k1 = (n + 1 < p_in) ? n + 1 : p_in;
-            if (OP == OP_L2L) k0 = n;
-            T ar = T(0), ai = T(0);
-            int xi = k0 * (k0 + 1) / 2 + m;
-            if (m == 0) {
-                for (int k = k0; k < k1; ++k) { ar = fma_t(ldt(Tr + k), Xre[xi], ar); xi += k + 1; }
-            } else {
-                for (int k = k0; k < k1; ++k) {
-                    const T t = ldt(Tr + k);
-                    ar = fma_t(t, Xre[xi], ar);
-                    ai = fma_t(t, Xim[xi], ai);
-                    xi += k + 1;
-                }
-            }
-            Are[m] = ar; Aim[m] = ai;
-        }
+        int m0 = 0;
+        for (; m0 + 3 <= n; m0 += 4) ztrans_block<T, OP, 4>(Tz, Pm, n, m0, p_in, Xre, Xim, Are, Aim);
+        if (m0 + 1 <= n) { ztrans_block<T, OP, 2>(Tz, Pm, n, m0, p_in, Xre, Xim, Are, Aim); m0 += 2; }
+        if (m0 <= n) ztrans_block<T, OP, 1>(Tz, Pm, n, m0, p_in, Xre, Xim, Are, Aim);
         // swap, rotate by -beta, swap
         swap_row(tb, n, Are, Aim, Bre, Bim, n + 1);
         for (int m = 1; m <= n; ++m) {
@@ -234,15 +300,23 @@ struct LaneStore {
     }
 };
 
+// Work distribution: the units (translations or targets) are cut into chunks
+// of 32, one per warp, handed out round-robin over a persistent grid sized to
+// the resident capacity.  Callers order units by decreasing cost, so the
+// round-robin deal balances the warps.
 template <typename T, int OP, bool XG>
-__global__ void __launch_bounds__(256) batch_kernel(DevTables<T> tb, const T *const *in,
+__global__ void __launch_bounds__(256, 1) batch_kernel(DevTables<T> tb, const T *const *in,
                                                     T *const *out, const T *shift, int p_in,
                                                     int p_out, long long count, int accumulate,
                                                     T *scratch, int *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LaneStore<T, XG> ls(reinterpret_cast<T *>(smem_raw), scratch, p_in, p_out);
-    const long long stride = XG ? (long long)gridDim.x * blockDim.x : count;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    const int lane = threadIdx.x & (WARP - 1);
+    const long long nw = (long long)gridDim.x * (blockDim.x / WARP);
+    for (long long c = (long long)blockIdx.x * (blockDim.x / WARP) + threadIdx.x / WARP;
+         c * WARP < count; c += nw) {
+        const long long i = c * WARP + lane;
+        if (i >= count) continue;
         const T *src = in[i];
         T *dst = out[i];
         if (src == nullptr || dst == nullptr) { atomicOr(status, STATUS_NULL_POINTER); continue; }
@@ -251,15 +325,19 @@ __global__ void __launch_bounds__(256) batch_kernel(DevTables<T> tb, const T *co
 }
 
 template <typename T, int OP, bool XG>
-__global__ void __launch_bounds__(256) lists_kernel(DevTables<T> tb, const T *const *src,
+__global__ void __launch_bounds__(256, 1) lists_kernel(DevTables<T> tb, const T *const *src,
                                                     const T *shift, const long long *offsets,
                                                     T *const *out, int p_in, int p_out,
                                                     long long n_targets, int accumulate,
                                                     T *scratch, int *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LaneStore<T, XG> ls(reinterpret_cast<T *>(smem_raw), scratch, p_in, p_out);
-    const long long stride = XG ? (long long)gridDim.x * blockDim.x : n_targets;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n_targets; t += stride) {
+    const int lane = threadIdx.x & (WARP - 1);
+    const long long nw = (long long)gridDim.x * (blockDim.x / WARP);
+    for (long long c = (long long)blockIdx.x * (blockDim.x / WARP) + threadIdx.x / WARP;
+         c * WARP < n_targets; c += nw) {
+        const long long t = c * WARP + lane;
+        if (t >= n_targets) continue;
         T *dst = out[t];
         const long long j0 = offsets[t], j1 = offsets[t + 1];
         if (dst == nullptr) { atomicOr(status, STATUS_NULL_POINTER); continue; }
