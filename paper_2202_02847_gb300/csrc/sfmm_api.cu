@@ -3,35 +3,18 @@
 
 #include <cstdlib>
 #include <cstring>
-#include <mutex>
 #include <new>
 #include <vector>
 
 #include "sfmm.h"
+#include "sfmm_ctx.h"
 #include "sfmm_kernels.cuh"
 #include "sfmm_tables.h"
+#include "sfmm_unrolled.cuh"
+#include "sfmm_unrolled_dispatch.h"
 
 using namespace sfmm;
 
-struct sfmm_ctx {
-    int Pmax = 0;
-    sfmm_dtype dtype = SFMM_F64;
-    int device = 0;
-    int sm_count = 0;
-    size_t smem_optin = 0;      // max dynamic shared memory per block
-    void *d_tables = nullptr;   // one allocation holding every table
-    int *d_status = nullptr;    // device status word (atomicOr by kernels)
-    DevTables<double> t64{};
-    DevTables<float> t32{};
-    // global scratch for orders whose rotated solid does not fit in shared
-    // memory: one slot of x_elems(P_max) elements per lane of a resident warp
-    void *d_scratch = nullptr;
-    size_t scratch_bytes = 0;
-    // launches that use the scratch are ordered through this event so that
-    // calls on different streams never share it concurrently
-    std::mutex scratch_mu;
-    cudaEvent_t scratch_free = nullptr;
-};
 
 namespace {
 
@@ -94,6 +77,40 @@ sfmm_status upload(const HostTables &ht, sfmm_ctx *h, DevTables<T> *dt) {
     dt->Grow = di + ht.Pmax + 1;
     dt->Pmax = ht.Pmax;
     return SFMM_OK;
+}
+
+// The unrolled kernels read their tables from __constant__ memory, one copy
+// per module and device; fill them once per device (at the first create).
+constexpr int kMaxDevices = 64;
+std::mutex g_const_mu;
+bool g_const_filled[kMaxDevices] = {};
+
+sfmm_status fill_unrolled_constants(int dev, size_t smem_optin) {
+    if (dev < 0 || dev >= kMaxDevices) return SFMM_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_const_mu);
+    if (g_const_filled[dev]) return SFMM_OK;
+    HostTables ht;
+    // layout of sfmm_unrolled.cuh: packed F and G of rows n < PC, c, 1/c and the
+    // three z-translation block sets, all built for order PC
+    if (build_tables(unrolled::PC, &ht) != 0) return SFMM_ERR_ORDER;
+    std::vector<double> t;
+    const int nF = unrolled::FR(unrolled::PC), nG = unrolled::GR(unrolled::PC);
+    t.insert(t.end(), ht.F.begin(), ht.F.begin() + nF);
+    t.insert(t.end(), ht.G.begin(), ht.G.begin() + nG);
+    t.insert(t.end(), ht.c.begin(), ht.c.end());
+    t.insert(t.end(), ht.ic.begin(), ht.ic.end());
+    for (int op = 0; op < 3; ++op) t.insert(t.end(), ht.Tz[op].begin(), ht.Tz[op].end());
+    if ((int)t.size() != unrolled::table_size()) return SFMM_ERR_UNSUPPORTED;
+    std::vector<float> t32(t.begin(), t.end());
+    if (!unrolled::fill_constants(t.data(), t32.data())) return SFMM_ERR_CUDA;
+    unrolled::set_attributes(smem_optin);
+    if (cudaGetLastError() != cudaSuccess) return SFMM_ERR_CUDA;
+    g_const_filled[dev] = true;
+    return SFMM_OK;
+}
+
+unrolled::Launch launch_info(const sfmm_ctx *h, cudaStream_t s) {
+    return unrolled::Launch{h->sm_count, h->smem_optin, h->d_status, s};
 }
 
 sfmm_status check_common(sfmm_handle h, int p_in, int p_out, long long count) {
@@ -269,6 +286,9 @@ sfmm_status batch(sfmm_handle h, int op, const void *const *in, void *const *out
     if (count == 0) return SFMM_OK;
     if (in == nullptr || out == nullptr || shift == nullptr) return SFMM_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (p_in == p_out && unrolled::compiled(p_in) && h->unrolled_ok)
+        return unrolled::launch_batch(h->dtype == SFMM_F64, p_in, op, in, out, shift, count,
+                                      accumulate, launch_info(h, s)) ? SFMM_OK : SFMM_ERR_CUDA;
     if (h->dtype == SFMM_F64)
         return launch_batch<double>(h, op, in, out, shift, p_in, p_out, count, accumulate, s, h->t64);
     return launch_batch<float>(h, op, in, out, shift, p_in, p_out, count, accumulate, s, h->t32);
@@ -334,6 +354,10 @@ sfmm_status sfmm_create(int P_max, sfmm_dtype dtype, sfmm_handle *out) {
         }
     }
     if (st == SFMM_OK) {
+        st = fill_unrolled_constants(dev, h->smem_optin);
+        h->unrolled_ok = (st == SFMM_OK);
+    }
+    if (st == SFMM_OK) {
         if (dtype == SFMM_F64) set_kernel_attrs<double>(h->smem_optin);
         else set_kernel_attrs<float>(h->smem_optin);
         if (cudaGetLastError() != cudaSuccess) st = SFMM_ERR_CUDA;
@@ -396,6 +420,9 @@ sfmm_status sfmm_translate_lists(sfmm_handle h, sfmm_op op, const void *const *s
     if (n_targets == 0) return SFMM_OK;
     if (src == nullptr || shift == nullptr || offsets == nullptr || out == nullptr) return SFMM_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (p_in == p_out && unrolled::compiled(p_in) && h->unrolled_ok)
+        return unrolled::launch_lists(h->dtype == SFMM_F64, p_in, (int)op, src, shift, offsets, out,
+                                      n_targets, accumulate, launch_info(h, s)) ? SFMM_OK : SFMM_ERR_CUDA;
     if (h->dtype == SFMM_F64)
         return launch_lists<double>(h, (int)op, src, shift, offsets, out, p_in, p_out, n_targets, accumulate, s, h->t64);
     return launch_lists<float>(h, (int)op, src, shift, offsets, out, p_in, p_out, n_targets, accumulate, s, h->t32);

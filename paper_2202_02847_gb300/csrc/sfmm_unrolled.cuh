@@ -1,0 +1,391 @@
+// Fully unrolled translation kernels for fixed orders p_in = p_out = P <= 12.
+//
+// Same algorithm as sfmm_kernels.cuh (Sec. 3.4 steps 1-4 with the
+// orthonormal-basis tables), specialised at compile time so that
+//   * the row buffers and the powers of e^{i alpha}, e^{i beta} live in
+//     registers and every table entry is a __constant__ operand at a
+//     compile-time offset (no address arithmetic, no table loads in L1);
+//   * only the solid itself stays in shared memory (P(P+1) reals per thread,
+//     interleaved across the warp with an odd stride, conflict-free for
+//     per-lane and for cooperative accesses), which lets 8 warps share an SM
+//     at P = 10 in FP64.  GB300's FP64 pipe issues one warp
+//     instruction per 64 cycles per SM sub-partition with a 64-cycle dependent
+//     latency, so two warps per sub-partition keep it busy while the other
+//     waits on memory;
+//   * the solid is transformed in place: input rows are rotated into the
+//     rotated frame row by row, the z-axis translation replaces it column by
+//     column, and the rotation back replaces it row by row;
+//   * solids move between global and shared memory with coalesced
+//     warp-cooperative copies.
+// Lists run one group of G lanes per target (G = 32 for long M2L lists, 8 for
+// the 8 children of an M2M parent): each member translates one source per
+// round and the group sums its members' results in a fixed order.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "sfmm_kernels.cuh"
+#include "sfmm_tables.h"
+
+namespace sfmm {
+namespace unrolled {
+
+constexpr int PC = 12;   // largest compiled order; the constant tables cover n < PC
+
+// ---- packed table geometry (must match the host packing in sfmm_tables.cpp)
+__host__ __device__ constexpr int cF(int n, int m) { return (n - ((n + m) & 1)) / 2 + 1; }
+__host__ __device__ constexpr int l0G(int n, int m) { return ((n + m + 1) & 1) ? 1 : 2; }
+__host__ __device__ constexpr int cG(int n, int m) {
+    return (m == 0 || n < l0G(n, m)) ? 0 : (n - l0G(n, m)) / 2 + 1;
+}
+__host__ __device__ constexpr int FM(int n, int m) {
+    int s = 0;
+    for (int i = 0; i < m; ++i) s += cF(n, i);
+    return s;
+}
+__host__ __device__ constexpr int GM(int n, int m) {
+    int s = 0;
+    for (int i = 1; i < m; ++i) s += cG(n, i);
+    return s;
+}
+__host__ __device__ constexpr int FR(int n) {
+    int s = 0;
+    for (int i = 0; i < n; ++i) s += FM(i, i + 1);
+    return s;
+}
+__host__ __device__ constexpr int GR(int n) {
+    int s = 0;
+    for (int i = 0; i < n; ++i) s += GM(i, i + 1);
+    return s;
+}
+__host__ __device__ constexpr int QT(int P) {
+    int s = 0;
+    for (int m = 0; m < P; ++m) s += (P - m) * (P - m);
+    return s;
+}
+__host__ __device__ constexpr int TB(int m) {       // start of z-translation block m
+    int s = 0;
+    for (int i = 0; i < m; ++i) s += (PC - i) * (PC - i);
+    return s;
+}
+
+constexpr int OFF_F = 0;
+constexpr int OFF_G = OFF_F + FR(PC);
+constexpr int OFF_C = OFF_G + GR(PC);
+constexpr int OFF_IC = OFF_C + PC * (PC + 1) / 2;
+constexpr int OFF_T = OFF_IC + PC * (PC + 1) / 2;
+constexpr int NTAB = OFF_T + 3 * QT(PC);
+
+// One copy per translation unit (each unit is its own module); filled by
+// fill_constants() of that unit.
+static __constant__ double c_tab64[NTAB];
+static __constant__ float c_tab32[NTAB];
+
+template <typename T>
+__device__ __forceinline__ T ct(int i);
+template <>
+__device__ __forceinline__ double ct<double>(int i) { return c_tab64[i]; }
+template <>
+__device__ __forceinline__ float ct<float>(int i) { return c_tab32[i]; }
+
+// Warp-level fence: keeps the instruction scheduler from hoisting the shared-memory
+// traffic of one row (or column) above the previous one, which would keep
+// several rows alive in registers at once.
+__device__ __forceinline__ void fence() { __syncwarp(); }
+
+// Per-lane view of the warp's solid area: element e of lane j at e*33 + j.
+// The odd stride keeps both access patterns conflict-free (a lane walking its
+// own solid, and the warp copying one solid with consecutive elements per
+// lane), and a lane's addresses are its base plus compile-time offsets.
+constexpr int XSTRIDE = 33;
+template <typename T>
+struct Sw {
+    T *wb;      // warp base
+    int lane;
+    __device__ __forceinline__ T &operator[](int e) const { return wb[e * XSTRIDE + lane]; }
+    __device__ __forceinline__ T &at(int e, int j) const { return wb[e * XSTRIDE + j]; }
+};
+
+// One axis swap of row N (eq. Mswapxz / FGmappings) on register rows.
+template <typename T, int N>
+__device__ __forceinline__ void swap_u(const T *ir, const T *ii, T *orr, T *oi) {
+#pragma unroll
+    for (int m = 0; m <= N; ++m) {
+        T acc = T(0);
+        int i = 0;
+#pragma unroll
+        for (int l = (N + m) & 1; l <= N; l += 2, ++i)
+            acc = fma_t(ct<T>(OFF_F + FR(N) + FM(N, m) + i), ir[l], acc);
+        orr[m] = acc;
+    }
+    oi[0] = T(0);
+#pragma unroll
+    for (int m = 1; m <= N; ++m) {
+        T acc = T(0);
+        int i = 0;
+#pragma unroll
+        for (int l = l0G(N, m); l <= N; l += 2, ++i)
+            acc = fma_t(ct<T>(OFF_G + GR(N) + GM(N, m) + i), ii[l], acc);
+        oi[m] = acc;
+    }
+}
+
+// Rotation powers of one translation: e^{i m alpha} and e^{i m beta}, m < P.
+template <typename T, int P>
+struct Powers {
+    T ar[P], ai[P], br[P], bi[P];
+};
+
+// Input row N: scale, orthonormal basis, rotate alpha, swap, rotate beta, swap.
+template <typename T, int P, int OP, int N>
+__device__ __forceinline__ void rows_in(Sw<T> X, const Powers<T, P> &pw, T s, T step) {
+    if constexpr (N < P) {
+        constexpr int o = N * (N + 1);
+        T ar[N + 1], ai[N + 1], br[N + 1], bi[N + 1];
+#pragma unroll
+        for (int m = 0; m <= N; ++m) {
+            const T f = s * ct<T>((OP == OP_L2L ? OFF_IC : OFF_C) + N * (N + 1) / 2 + m);
+            const T re = X[o + m] * f, im = X[o + N + 1 + m] * f;
+            ar[m] = re * pw.ar[m] - im * pw.ai[m];
+            ai[m] = fma_t(re, pw.ai[m], im * pw.ar[m]);
+        }
+        swap_u<T, N>(ar, ai, br, bi);
+#pragma unroll
+        for (int m = 1; m <= N; ++m) {
+            const T re = br[m], im = bi[m];
+            br[m] = re * pw.br[m] - im * pw.bi[m];
+            bi[m] = fma_t(re, pw.bi[m], im * pw.br[m]);
+        }
+        swap_u<T, N>(br, bi, ar, ai);
+#pragma unroll
+        for (int m = 0; m <= N; ++m) { X[o + m] = ar[m]; X[o + N + 1 + m] = ai[m]; }
+    }
+}
+
+// z-axis translation of column M in place (eq. zm2lkernels for M2L).
+template <typename T, int P, int OP, int M>
+__device__ __forceinline__ void columns_z(Sw<T> X) {
+    if constexpr (M < P) {
+        T xr[P - M], xi[P - M];
+#pragma unroll
+        for (int k = M; k < P; ++k) { xr[k - M] = X[k * (k + 1) + M]; xi[k - M] = X[k * (k + 1) + k + 1 + M]; }
+#pragma unroll
+        for (int n = M; n < P; ++n) {
+            const int kb = (OP == OP_L2L) ? n : M;
+            const int ke = (OP == OP_M2M) ? n + 1 : P;
+            T accr = T(0), acci = T(0);
+#pragma unroll
+            for (int k = kb; k < ke; ++k) {
+                const T t = ct<T>(OFF_T + OP * QT(PC) + TB(M) + (n - M) * (PC - M) + (k - M));
+                accr = fma_t(t, xr[k - M], accr);
+                if (M > 0) acci = fma_t(t, xi[k - M], acci);
+            }
+            X[n * (n + 1) + M] = accr;
+            X[n * (n + 1) + n + 1 + M] = acci;
+        }
+    }
+}
+
+// Output row N: swap, rotate -beta, swap, rotate -alpha, undo basis and scaling.
+template <typename T, int P, int OP, int N>
+__device__ __forceinline__ void rows_out(Sw<T> X, const Powers<T, P> &pw, T so, T step) {
+    if constexpr (N < P) {
+        constexpr int o = N * (N + 1);
+        T ar[N + 1], ai[N + 1], br[N + 1], bi[N + 1];
+#pragma unroll
+        for (int m = 0; m <= N; ++m) { ar[m] = X[o + m]; ai[m] = X[o + N + 1 + m]; }
+        swap_u<T, N>(ar, ai, br, bi);
+#pragma unroll
+        for (int m = 1; m <= N; ++m) {
+            const T re = br[m], im = bi[m];
+            br[m] = fma_t(re, pw.br[m], im * pw.bi[m]);
+            bi[m] = im * pw.br[m] - re * pw.bi[m];
+        }
+        swap_u<T, N>(br, bi, ar, ai);
+#pragma unroll
+        for (int m = 0; m <= N; ++m) {
+            const T f = so * ct<T>((OP == OP_M2M ? OFF_IC : OFF_C) + N * (N + 1) / 2 + m);
+            const T re = ar[m] * f, im = ai[m] * f;
+            X[o + m] = fma_t(re, pw.ar[m], im * pw.ai[m]);
+            X[o + N + 1 + m] = im * pw.ar[m] - re * pw.ai[m];
+        }
+    }
+}
+
+template <typename T, int P, int OP, int K>
+__device__ __forceinline__ void step_switch(int st, Sw<T> X, const Powers<T, P> &pw, T s, T so) {
+    if constexpr (K < 3 * P) {
+        if (st == K) {
+            if constexpr (K < P) rows_in<T, P, OP, K>(X, pw, s, T(0));
+            else if constexpr (K < 2 * P) columns_z<T, P, OP, K - P>(X);
+            else rows_out<T, P, OP, K - 2 * P>(X, pw, so, T(0));
+        } else {
+            step_switch<T, P, OP, K + 1>(st, X, pw, s, so);
+        }
+    }
+}
+
+// One translation of order P by the calling thread, in place on its solid X.
+template <typename T, int P, int OP>
+__device__ __forceinline__ void translate_u(Sw<T> X, T x, T y, T z) {
+    const T rho2 = x * x + y * y;
+    const T R = sqrt_t(rho2 + z * z);
+    if (OP != OP_M2L && !(R > T(0))) return;            // zero shift: identity
+    const T rho = sqrt_t(rho2);
+    T ca = T(1), sa = T(0);                               // cos(alpha) = y/rho, sin(alpha) = x/rho
+    if (rho > T(0)) { const T ir = T(1) / rho; ca = y * ir; sa = x * ir; }
+    const T iR = T(1) / R;
+    const T cb = z * iR, sb = -rho * iR;                  // cos(beta) = z/|r|, sin(beta) = -rho/|r|
+    Powers<T, P> pw;
+    pw.ar[0] = T(1); pw.ai[0] = T(0); pw.br[0] = T(1); pw.bi[0] = T(0);
+#pragma unroll
+    for (int m = 1; m < P; ++m) {
+        pw.ar[m] = pw.ar[m - 1] * ca - pw.ai[m - 1] * sa;
+        pw.ai[m] = fma_t(pw.ar[m - 1], sa, pw.ai[m - 1] * ca);
+        pw.br[m] = pw.br[m - 1] * cb - pw.bi[m - 1] * sb;
+        pw.bi[m] = fma_t(pw.br[m - 1], sb, pw.bi[m - 1] * cb);
+    }
+    // One basic block per row / column step: a runtime loop over the steps
+    // with a switch keeps the instruction scheduler from interleaving steps
+    // (which would keep several rows of tables and data alive at once).
+    T s = (OP == OP_M2L) ? iR : T(1);                   // input scale |r|^{-(n+1)}, ^{-n}, ^{n}
+    const T step_in = (OP == OP_L2L) ? R : iR;
+    T so = T(1);                                       // output scale
+    const T step_out = (OP == OP_M2M) ? R : iR;
+#pragma unroll 1
+    for (int st = 0; st < 3 * P; ++st) {
+        step_switch<T, P, OP, 0>(st, X, pw, s, so);
+        if (st < P) s *= step_in;
+        else if (st >= 2 * P) so *= step_out;
+    }
+}
+
+// Copy the 32 solids of the warp's lanes from global memory into the
+// swizzled area (null pointer: zeros).  All 32 lanes take part.
+template <typename T, int S>
+__device__ __forceinline__ void load_solids(Sw<T> X, const T *mine) {
+#pragma unroll 4
+    for (int j = 0; j < 32; ++j) {
+        const T *p = reinterpret_cast<const T *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(mine), j));
+#pragma unroll
+        for (int e0 = 0; e0 < S; e0 += 32) {
+            const int e = e0 + X.lane;
+            if (e < S) X.at(e, j) = p ? __ldg(p + e) : T(0);
+        }
+    }
+}
+
+template <typename T, int P, int OP>
+__global__ void __launch_bounds__(256, 1) ubatch_kernel(const T *const *in, T *const *out,
+                                                        const T *shift, long long count,
+                                                        int accumulate, int *status) {
+    constexpr int S = P * (P + 1);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Sw<T> X{reinterpret_cast<T *>(smem_raw) + (size_t)warp * S * XSTRIDE, lane};
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + warp; c * 32 < count; c += nw) {
+        const long long i = c * 32 + lane;
+        const bool valid = i < count;
+        const T *src = valid ? in[i] : nullptr;
+        T *dst = valid ? out[i] : nullptr;
+        if (valid && (src == nullptr || dst == nullptr)) {
+            atomicOr(status, STATUS_NULL_POINTER);
+            src = nullptr;
+            dst = nullptr;
+        }
+        load_solids<T, S>(X, src);
+        __syncwarp();
+        T x = T(0), y = T(0), z = T(1);
+        if (src) { x = shift[3 * i]; y = shift[3 * i + 1]; z = shift[3 * i + 2]; }
+        translate_u<T, P, OP>(X, x, y, z);
+        __syncwarp();
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+            T *p = reinterpret_cast<T *>(
+                __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(dst), j));
+            if (p == nullptr) continue;
+#pragma unroll
+            for (int e0 = 0; e0 < S; e0 += 32) {
+                const int e = e0 + lane;
+                if (e < S) {
+                    T v = X.at(e, j);
+                    if (accumulate) v += p[e];
+                    p[e] = v;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Target-major CSR lists, one group of G lanes per target, sources dealt to
+// the members in rounds of G; each round's G results are summed per
+// coefficient in member order and added to the group's running sum.
+template <typename T, int P, int OP, int G>
+__global__ void __launch_bounds__(256, 1) ulists_kernel(const T *const *src, const T *shift,
+                                                        const long long *offsets, T *const *out,
+                                                        long long n_targets, int accumulate,
+                                                        int *status) {
+    constexpr int S = P * (P + 1);
+    constexpr int NG = 32 / G;                 // groups per warp
+    constexpr int NA = (S + G - 1) / G;        // coefficients per member
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = lane / G, mem = lane % G;
+    Sw<T> X{reinterpret_cast<T *>(smem_raw) + (size_t)warp * S * XSTRIDE, lane};
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + warp; c * NG < n_targets; c += nw) {
+        const long long t = c * NG + q;
+        long long j0 = 0, j1 = 0;
+        if (t < n_targets) {
+            j0 = offsets[t];
+            j1 = offsets[t + 1];
+            if (j1 < j0) { atomicOr(status, STATUS_BAD_OFFSETS); j1 = j0; }
+        }
+        int rounds = (int)((j1 - j0 + G - 1) / G);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) rounds = max(rounds, __shfl_xor_sync(0xffffffffu, rounds, d));
+        T acc[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) acc[a] = T(0);
+        for (int r = 0; r < rounds; ++r) {
+            const long long j = j0 + (long long)r * G + mem;
+            const T *s = (j < j1) ? src[j] : nullptr;
+            if (j < j1 && s == nullptr) atomicOr(status, STATUS_NULL_POINTER);
+            load_solids<T, S>(X, s);
+            __syncwarp();
+            T x = T(0), y = T(0), z = T(1);
+            if (s) { x = shift[3 * j]; y = shift[3 * j + 1]; z = shift[3 * j + 2]; }
+            translate_u<T, P, OP>(X, x, y, z);
+            __syncwarp();
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                const int e = mem + a * G;
+                if (e < S) {
+#pragma unroll
+                    for (int i = 0; i < G; ++i) acc[a] += X.at(e, q * G + i);
+                }
+            }
+            __syncwarp();
+        }
+        if (t < n_targets) {
+            T *dst = out[t];
+            if (dst == nullptr) {
+                atomicOr(status, STATUS_NULL_POINTER);
+            } else {
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    const int e = mem + a * G;
+                    if (e < S) dst[e] = accumulate ? dst[e] + acc[a] : acc[a];
+                }
+            }
+        }
+    }
+}
+
+}  // namespace unrolled
+}  // namespace sfmm

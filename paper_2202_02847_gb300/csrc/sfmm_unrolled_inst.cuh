@@ -1,0 +1,106 @@
+// Instantiation of the unrolled kernels for one order (SFMM_UNROLLED_P) and
+// one real type (SFMM_UNROLLED_T).  Included by one small translation unit per
+// (order, type), so the units compile in parallel.
+#include "sfmm_unrolled.cuh"
+#include "sfmm_unrolled_dispatch.h"
+
+#if !defined(SFMM_UNROLLED_P) || !defined(SFMM_UNROLLED_T) || !defined(SFMM_UNROLLED_NS)
+#error "define SFMM_UNROLLED_P, SFMM_UNROLLED_T and SFMM_UNROLLED_NS before including this file"
+#endif
+
+namespace sfmm {
+namespace unrolled {
+namespace SFMM_UNROLLED_NS {
+
+constexpr int P = SFMM_UNROLLED_P;
+constexpr int S = P * (P + 1);
+
+using Real = SFMM_UNROLLED_T;
+
+bool fill(const double *t64, const float *t32) {
+    if (std::is_same<Real, double>::value)
+        return cudaMemcpyToSymbol(c_tab64, t64, sizeof(double) * NTAB) == cudaSuccess;
+    return cudaMemcpyToSymbol(c_tab32, t32, sizeof(float) * NTAB) == cudaSuccess;
+}
+
+template <typename K>
+void attr(K k, size_t smem) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename T>
+void set_attrs_t(size_t smem) {
+    attr(ubatch_kernel<T, P, OP_M2M>, smem);
+    attr(ubatch_kernel<T, P, OP_M2L>, smem);
+    attr(ubatch_kernel<T, P, OP_L2L>, smem);
+    attr(ulists_kernel<T, P, OP_M2M, 8>, smem);
+    attr(ulists_kernel<T, P, OP_M2L, 32>, smem);
+    attr(ulists_kernel<T, P, OP_L2L, 8>, smem);
+}
+
+void set_attrs(size_t smem) { set_attrs_t<Real>(smem); }
+
+// warps per block and blocks for `chunks` warp-chunks of work
+template <typename T, typename K>
+bool geometry(K kernel, const Launch &L, long long chunks, int *warps, size_t *smem, long long *blocks) {
+    const size_t per_warp = (size_t)S * XSTRIDE * sizeof(T);
+    int w = (int)(L.smem_optin / per_warp);
+    if (w < 1) return false;
+    if (w > 8) w = 8;
+    *warps = w;
+    *smem = (size_t)w * per_warp;
+    long long b = (chunks + w - 1) / w;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, w * 32, *smem) != cudaSuccess || nb < 1)
+        nb = 1;
+    const long long cap = (long long)nb * L.sm_count;
+    *blocks = b < cap ? b : cap;
+    return *blocks >= 1;
+}
+
+template <typename T, int OP>
+bool batch_t(const void *const *in, void *const *out, const void *shift, long long count,
+             int accumulate, const Launch &L) {
+    auto k = ubatch_kernel<T, P, OP>;
+    int w;
+    size_t smem;
+    long long blocks;
+    if (!geometry<T>(k, L, (count + 31) / 32, &w, &smem, &blocks)) return false;
+    k<<<(unsigned)blocks, w * 32, smem, L.stream>>>(
+        reinterpret_cast<const T *const *>(in), reinterpret_cast<T *const *>(out),
+        reinterpret_cast<const T *>(shift), count, accumulate, L.status);
+    return cudaGetLastError() == cudaSuccess;
+}
+
+template <typename T, int OP, int G>
+bool lists_t(const void *const *src, const void *shift, const long long *offsets,
+             void *const *out, long long n_targets, int accumulate, const Launch &L) {
+    auto k = ulists_kernel<T, P, OP, G>;
+    int w;
+    size_t smem;
+    long long blocks;
+    const long long chunks = (n_targets + (32 / G) - 1) / (32 / G);
+    if (!geometry<T>(k, L, chunks, &w, &smem, &blocks)) return false;
+    k<<<(unsigned)blocks, w * 32, smem, L.stream>>>(
+        reinterpret_cast<const T *const *>(src), reinterpret_cast<const T *>(shift), offsets,
+        reinterpret_cast<T *const *>(out), n_targets, accumulate, L.status);
+    return cudaGetLastError() == cudaSuccess;
+}
+
+bool batch(int op, const void *const *in, void *const *out, const void *shift, long long count,
+           int accumulate, const Launch &L) {
+    if (op == OP_M2M) return batch_t<Real, OP_M2M>(in, out, shift, count, accumulate, L);
+    if (op == OP_M2L) return batch_t<Real, OP_M2L>(in, out, shift, count, accumulate, L);
+    return batch_t<Real, OP_L2L>(in, out, shift, count, accumulate, L);
+}
+
+bool lists(int op, const void *const *src, const void *shift, const long long *offsets,
+           void *const *out, long long n_targets, int accumulate, const Launch &L) {
+    if (op == OP_M2M) return lists_t<Real, OP_M2M, 8>(src, shift, offsets, out, n_targets, accumulate, L);
+    if (op == OP_M2L) return lists_t<Real, OP_M2L, 32>(src, shift, offsets, out, n_targets, accumulate, L);
+    return lists_t<Real, OP_L2L, 8>(src, shift, offsets, out, n_targets, accumulate, L);
+}
+
+}  // namespace SFMM_UNROLLED_NS
+}  // namespace unrolled
+}  // namespace sfmm

@@ -1,0 +1,79 @@
+// Registry of the compiled unrolled orders (see sfmm_unrolled_dispatch.h).
+#include "sfmm_unrolled.cuh"
+#include "sfmm_unrolled_dispatch.h"
+
+namespace sfmm {
+namespace unrolled {
+
+#define SFMM_DECLARE(NS)                                                                        \
+    namespace NS {                                                                              \
+    bool fill(const double *, const float *);                                                   \
+    void set_attrs(size_t);                                                                     \
+    bool batch(int, const void *const *, void *const *, const void *, long long, int,           \
+               const Launch &);                                                                 \
+    bool lists(int, const void *const *, const void *, const long long *, void *const *,        \
+               long long, int, const Launch &);                                                 \
+    }
+SFMM_DECLARE(p6_f64)
+SFMM_DECLARE(p8_f64)
+SFMM_DECLARE(p10_f64)
+SFMM_DECLARE(p12_f64)
+SFMM_DECLARE(p6_f32)
+SFMM_DECLARE(p8_f32)
+SFMM_DECLARE(p10_f32)
+SFMM_DECLARE(p12_f32)
+#undef SFMM_DECLARE
+
+bool compiled(int P) { return P == 6 || P == 8 || P == 10 || P == 12; }
+
+int table_size() { return NTAB; }
+
+bool fill_constants(const double *t64, const float *t32) {
+    return p6_f64::fill(t64, t32) && p8_f64::fill(t64, t32) && p10_f64::fill(t64, t32) &&
+           p12_f64::fill(t64, t32) && p6_f32::fill(t64, t32) && p8_f32::fill(t64, t32) &&
+           p10_f32::fill(t64, t32) && p12_f32::fill(t64, t32);
+}
+
+void set_attributes(size_t smem) {
+    p6_f64::set_attrs(smem);
+    p8_f64::set_attrs(smem);
+    p10_f64::set_attrs(smem);
+    p12_f64::set_attrs(smem);
+    p6_f32::set_attrs(smem);
+    p8_f32::set_attrs(smem);
+    p10_f32::set_attrs(smem);
+    p12_f32::set_attrs(smem);
+}
+
+#define SFMM_PICK(P, F64, CALL)                                 \
+    if (F64) {                                                  \
+        switch (P) {                                            \
+            case 6: return p6_f64::CALL;                        \
+            case 8: return p8_f64::CALL;                        \
+            case 10: return p10_f64::CALL;                      \
+            case 12: return p12_f64::CALL;                      \
+        }                                                       \
+    } else {                                                    \
+        switch (P) {                                            \
+            case 6: return p6_f32::CALL;                        \
+            case 8: return p8_f32::CALL;                        \
+            case 10: return p10_f32::CALL;                      \
+            case 12: return p12_f32::CALL;                      \
+        }                                                       \
+    }                                                           \
+    return false;
+
+bool launch_batch(bool f64, int P, int op, const void *const *in, void *const *out,
+                  const void *shift, long long count, int accumulate, const Launch &L) {
+    SFMM_PICK(P, f64, batch(op, in, out, shift, count, accumulate, L))
+}
+
+bool launch_lists(bool f64, int P, int op, const void *const *src, const void *shift,
+                  const long long *offsets, void *const *out, long long n_targets,
+                  int accumulate, const Launch &L) {
+    SFMM_PICK(P, f64, lists(op, src, shift, offsets, out, n_targets, accumulate, L))
+}
+#undef SFMM_PICK
+
+}  // namespace unrolled
+}  // namespace sfmm

@@ -104,10 +104,10 @@ def test_high_orders(sf, orc, h64, op, P):
     assert U.rel_err(got, want, P, U.out_kind(op)) <= TOL["f64"]
 
 
+@pytest.mark.parametrize("P", [7, 10])
 @pytest.mark.parametrize("count", [1, 31, 33, 257])
-def test_ragged_counts(sf, orc, h64, count):
+def test_ragged_counts(sf, orc, h64, count, P):
     g = W.rng(3000 + count)
-    P = 7
     C = W.random_solids(g, count, P)
     sh = W.shifts(g, count)
     got = U.run_batch(sf, h64, "m2l", C, sh, P, P, "f64")
@@ -119,11 +119,11 @@ def test_count_zero_is_noop(sf, h64):
     sf.m2l_batch(h64, 0, 0, 0, 4, 4, 0)
 
 
+@pytest.mark.parametrize("P", [9, 10])
 @pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
-def test_special_shifts(sf, orc, h64, op):
+def test_special_shifts(sf, orc, h64, op, P):
     """Shifts along +z and -z (rho = 0, cos(alpha) = 1 by the special case of
     Sec. 3.4 step 1), nearly axial shifts, and axis-aligned shifts."""
-    P = 9
     sh = np.array([[0, 0, 3.0], [0, 0, -2.5], [1e-170, 0, 3.0], [0, 1e-9, -2.2],
                    [3.0, 0, 0], [0, -2.4, 0], [2.0, 2.0, 0], [-1.5, 0, 1.5]])
     g = W.rng(4000)
@@ -169,7 +169,7 @@ def test_result_independent_of_batch(sf, h64):
 
 
 @pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
-@pytest.mark.parametrize("P", [6, 10])
+@pytest.mark.parametrize("P", [6, 7, 10, 12])
 def test_fp32(sf, orc, h32, op, P):
     g = W.rng(5000 + P)
     count = 200
@@ -180,6 +180,57 @@ def test_fp32(sf, orc, h32, op, P):
     want, _ = orc.batch(op, P, P, C.astype(np.float32).astype(np.float64),
                         sh.astype(np.float32).astype(np.float64))
     assert U.rel_err(got, want, P, U.out_kind(op)) <= TOL["f32"]
+
+
+def _run_lists(sf, orc, h, op, P_in, P_out, accumulate, seed, dtype="f64", maxlen=40, nt=70):
+    import torch
+    g = W.rng(seed)
+    lens = g.integers(0, maxlen + 1, size=nt)
+    lens[3] = 0
+    offs = np.zeros(nt + 1, np.int64)
+    np.cumsum(lens, out=offs[1:])
+    nnz = int(offs[-1])
+    nsrc = 90
+    S = W.random_solids(g, nsrc, P_in)
+    src_idx = g.integers(0, nsrc, size=nnz)
+    sh = W.shifts(g, nnz)
+    init = W.random_solids(g, nt, P_out)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    if dtype == "f32":
+        S, sh, init = (a.astype(np.float32).astype(np.float64) for a in (S, sh, init))
+    dev = "cuda"
+    dS = torch.tensor(S, device=dev, dtype=tdt)
+    dO = torch.tensor(init, device=dev, dtype=tdt)
+    psrc = sf.pointer_array(dS, P_in * (P_in + 1), torch.tensor(src_idx))
+    pout = sf.pointer_array(dO, P_out * (P_out + 1), torch.arange(nt))
+    sf.translate_lists(h, op, psrc, torch.tensor(sh, device=dev, dtype=tdt),
+                       torch.tensor(offs, device=dev), pout, P_in, P_out, nt,
+                       accumulate=accumulate)
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    got = dO.double().cpu().numpy()
+    each, _ = orc.batch(op, P_in, P_out, S[src_idx], sh)
+    want = init.copy() if accumulate else np.zeros_like(init)
+    for t in range(nt):
+        for j in range(offs[t], offs[t + 1]):
+            want[t] += each[j]
+    return U.rel_err(got, want, P_out, U.out_kind(op))
+
+
+@pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
+@pytest.mark.parametrize("accumulate", [False, True])
+@pytest.mark.parametrize("P", [6, 8, 10, 12])
+def test_lists_fixed_orders(sf, orc, h64, op, accumulate, P):
+    """Lists at the orders with fully unrolled kernels (groups of 8 or 32 lanes
+    per target, lengths 0..70 so that targets take several rounds)."""
+    err = _run_lists(sf, orc, h64, op, P, P, accumulate, 6100 + P, maxlen=70)
+    assert err <= TOL["f64"], err
+
+
+@pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
+def test_lists_fixed_orders_fp32(sf, orc, h32, op):
+    err = _run_lists(sf, orc, h32, op, 10, 10, False, 6200, dtype="f32")
+    assert err <= TOL["f32"], err
 
 
 @pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
@@ -219,9 +270,9 @@ def test_lists(sf, orc, h64, op, accumulate):
     assert U.rel_err(got, want, P_out, U.out_kind(op)) <= TOL["f64"]
 
 
-def test_device_status_reports_null_pointer(sf, h64):
+@pytest.mark.parametrize("P", [4, 6])
+def test_device_status_reports_null_pointer(sf, h64, P):
     import torch
-    P = 4
     cin = torch.zeros(2, P * (P + 1), dtype=torch.float64, device="cuda")
     cout = torch.zeros_like(cin)
     pin = sf.pointer_array(cin, P * (P + 1), torch.arange(2))
