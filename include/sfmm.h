@@ -180,6 +180,37 @@ sfmm_status sfmm_p2l_boxes(sfmm_handle h, int P, const void *points, const void 
 sfmm_status sfmm_sync_status(sfmm_handle h, sfmm_stream stream, int *device_status);
 
 /*
+ * Batched translations that allocate nothing (the paper has no counterpart;
+ * this is an interface for callers that cannot allocate device memory where
+ * they translate: code running while a stream is captured into a CUDA graph,
+ * a host framework that hands out a fixed device-memory budget, or a real-time
+ * loop where cudaMalloc/cudaFree and their implicit synchronisation are not
+ * allowed).  Same arguments and results as sfmm_m2m/m2l/l2l_batch with the
+ * op selected by `op`, computed by the global-scratch variant of the batch
+ * kernel whose scratch is a fixed 16 MiB device array inside the library
+ * (held by every GPU that loads the library until the process exits) instead
+ * of memory owned by the handle.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ * Limits: p_in, p_out in [1, P_max] (else SFMM_ERR_ORDER); one warp's slot of
+ * 32 p_in (p_in+1) reals must fit in the 16 MiB array, which holds for every
+ * order a handle accepts (else SFMM_ERR_UNSUPPORTED); fewer warps run at once
+ * when p_in is large, any count is served.
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and caches it; make that
+ * first call before any stream capture.  The current device must be the
+ * handle's device (else SFMM_ERR_ARG).
+ * Sharing: every call on a device uses the same array, which keeps the last
+ * call's contents (each thread overwrites its whole slot before reading it, so
+ * nothing needs clearing).  Calls whose kernels overlap on the GPU (different
+ * streams, any handle) race on the array: order them on one stream or with
+ * events.
+ */
+sfmm_status sfmm_translate_batch_noalloc(sfmm_handle h, sfmm_op op, const void *const *in,
+                                         void *const *out, const void *shift, int p_in,
+                                         int p_out, long long count, int accumulate,
+                                         sfmm_stream stream);
+
+/*
  * Host-side introspection of the precomputed tables (no GPU, no handle).
  * sfmm_host_swap_matrices: the dense reduced swap matrices F_n and G_n of
  * eq. FGmappings in the orthonormal basis (row m, column l, (n+1)^2 doubles

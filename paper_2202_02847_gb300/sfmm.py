@@ -46,6 +46,7 @@ _SIGS = {
     "sfmm_p2m_boxes": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _ll, _vp]),
     "sfmm_p2l_boxes": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _ll, _vp]),
     "sfmm_sync_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
+    "sfmm_translate_batch_noalloc": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _ll, _i, _vp]),
     "sfmm_host_swap_matrices": (_i, [_i, _dp, _dp]),
     "sfmm_host_ztranslate": (_i, [_i, _i, _i, _dp]),
 }
@@ -149,6 +150,16 @@ def l2l_batch(h, inp, out, shift, p_in, p_out, count, accumulate=False, stream=N
 
 def translate_batch(op, h, *args, **kw):
     {"m2m": m2m_batch, "m2l": m2l_batch, "l2l": l2l_batch}[op](h, *args, **kw)
+
+
+def translate_batch_noalloc(h, op, inp, out, shift, p_in, p_out, count, accumulate=False,
+                            stream=None):
+    """sfmm_translate_batch_noalloc: like the *_batch calls, for callers that
+    cannot allocate device memory (scratch is a fixed array in the library)."""
+    _check(_lib.sfmm_translate_batch_noalloc(h.ptr, OPS.get(op, op), _addr(inp), _addr(out),
+                                             _addr(shift), int(p_in), int(p_out), int(count),
+                                             int(bool(accumulate)), _stream(stream)),
+           "sfmm_translate_batch_noalloc")
 
 
 def translate_lists(h, op, src, shift, offsets, out, p_in, p_out, n_targets,
