@@ -36,6 +36,8 @@ DEPTH, P, NPOINTS, SEED = 5, 10, 1 << 20, 2
 # GB300 FP64 pipe: 2 FMA/clk/SM (measured with a DFMA loop at >= 4 warps/SM,
 # matching the nominal 1.25 TFLOP/s) x 152 SMs x 2 FLOP x max SM clock.
 FP64_FMA_PER_CLK_SM = 2
+# FP32 pipe: 128 FMA/clk/SM (nominal; a FFMA loop measured 117 FMA/clk/SM).
+FP32_FMA_PER_CLK_SM = 128
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -260,6 +262,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0,
                     help="seconds of oracle work for the cpu_baseline leg")
     ap.add_argument("--no-oracle", action="store_true")
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"],
+                    help="f64: the plain FP64 workload (default); f32: the same pass in FP32")
     ap.add_argument("--depth", type=int, default=DEPTH,
                     help="octree depth (5 = the benchmark workload; smaller for profiling)")
     args = ap.parse_args()
@@ -281,8 +285,9 @@ def main():
 
     depth = args.depth
     tree = W.uniform_octree(depth, NPOINTS, seed=multirank.rank_seed(SEED, rank))
-    h = sfmm.Handle(P, "f64")
-    fp = UniformPass(tree, P, h, device=dev)
+    tdt = torch.float64 if args.dtype == "f64" else torch.float32
+    h = sfmm.Handle(P, args.dtype)
+    fp = UniformPass(tree, P, h, device=dev, dtype=tdt)
     fp.p2m_leaves(tree.points, tree.charges, tree.leaf_of_point)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -347,19 +352,23 @@ def main():
     if os.path.exists(peaks_path):
         sm_max = float(json.load(open(peaks_path)).get("sm_max_mhz", sm_max))
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = nsm * FP64_FMA_PER_CLK_SM * 2 * sm_max * 1e6
+    fma_clk = FP64_FMA_PER_CLK_SM if args.dtype == "f64" else FP32_FMA_PER_CLK_SM
+    peak = nsm * fma_clk * 2 * sm_max * 1e6
+    wbytes = 8 if args.dtype == "f64" else 4
     roof = {"bound": "alu", "achieved": flop / m2l_mean_s / 1e12, "peak": peak / 1e12,
             "unit": "TFLOP/s", "frac": flop / m2l_mean_s / peak,
-            "traffic": ncu_traffic(), "kernel": "lists_kernel<double, M2L> (one launch per step)",
+            "traffic": ncu_traffic() if args.dtype == "f64" else None,
+            "kernel": f"ulists_kernel<{'double' if args.dtype == 'f64' else 'float'}, P=10, M2L, G=32>"
+                      " (one launch per step)",
             "m2l_ms_mean": m2l_mean_s * 1e3,
-            "hbm_gbs_algorithmic": m2l_bytes(P) * m2l_per_step / m2l_mean_s / 1e9}
+            "hbm_gbs_algorithmic": m2l_bytes(P, wbytes) * m2l_per_step / m2l_mean_s / 1e9}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
         "data": "synthetic",
-        "config": {"workload": f"plain FP64 P=10: uniform octree level {depth} "
+        "config": {"workload": f"plain {args.dtype.upper()} P=10: uniform octree level {depth} "
                                f"({2 ** depth}^3 leaves), 1M uniform points, full M2M/M2L/L2L "
                                "translation pass",
                    "P": P, "depth": depth, "points_per_rank": NPOINTS,
@@ -377,12 +386,13 @@ def main():
         line["clocks"] = clocks
 
     if rank == 0 and not args.no_oracle and depth == DEPTH:
+        # the oracle is FP64; for FP32 runs the error is against it as well
         # device M2L result for sampled targets (M2L only, into a scratch copy)
         picks = sample_targets(fp, 24, 11)
         torch.cuda.synchronize()
         fp.m2l_all()
         torch.cuda.synchronize()
-        Lhost = fp.L.cpu().numpy()
+        Lhost = fp.L.double().cpu().numpy()
         dev_res = Lhost[fp.m2l_targets]
         err, rate, done, used = oracle_parity_and_rate(fp, tree, dev_res, picks, args.cpu_budget)
         line["rel_err_vs_oracle"] = {"weighted": err, "targets": len(picks),
