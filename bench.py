@@ -253,6 +253,156 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_batching(args):
+    """Batching workload: adaptive octree (<= 64 points per leaf) over a Plummer
+    sphere, P(level) = 4 + round(20 level / L_max), dual-tree M2L with theta =
+    0.5 (mixed p_in != p_out), FP64; launch policies and the fused/per-class
+    choice per M2L wave autotuned; the whole pass replayed as one CUDA graph."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_2202_02847_gb300 import sfmm, workloads as W
+    from paper_2202_02847_gb300.autotune import Autotuner
+    from paper_2202_02847_gb300.fmm import AdaptivePass
+    t_setup = time.perf_counter()
+    pts, q = W.plummer(args.points, seed=4)
+    tree = W.adaptive_octree(pts, leaf_size=64)
+    P_node = W.order_by_level(tree, lo=4, span=20)
+    h = sfmm.Handle(int(P_node.max()), "f64")
+    ap = AdaptivePass(tree, P_node, h)
+    ap.p2m_leaves(pts, q)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    tuner = Autotuner(h, "f64")
+    t0 = time.perf_counter()
+    chosen, waves = ap.autotune(tuner, reps=1)
+    tune_s = time.perf_counter() - t0
+    # per-phase times of one step outside the graph
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    stream = torch.cuda.current_stream()
+    ap.L.zero_()
+    ev[0].record(stream)
+    ap.upward()
+    ev[1].record(stream)
+    ap.m2l_all()
+    ev[2].record(stream)
+    ap.downward()
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    phase_ms = {"m2m": ev[0].elapsed_time(ev[1]), "m2l": ev[1].elapsed_time(ev[2]),
+                "l2l": ev[2].elapsed_time(ev[3])}
+    # the whole pass as one CUDA graph
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        ap.step()
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        ap.step()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            graph.replay()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    assert h.sync_status() == 0
+    total = sum(step_ms) * 1e-3
+    nm2l = ap.counts["m2l"]
+    flop = 0
+    for d in ap.waves:
+        offs = d["host"]["offs"]
+        for op, pi, po, tb, te in d["classes"]:
+            flop += m2l_flop(max(pi, po)) * int(offs[te] - offs[tb])
+    classes = sorted({(pi, po) for d in ap.waves for _, pi, po, _, _ in d["classes"]})
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = nsm * FP64_FMA_PER_CLK_SM * 2 * 2070e6
+    line = {
+        "metric": METRIC + " (batching: mixed-order adaptive pass)",
+        "value": nm2l * args.steps / total, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batching: adaptive octree (<=64/leaf) on a {args.points}-point "
+                               "Plummer sphere, P(level)=4+round(20 l/L), dual-tree M2L theta=0.5, "
+                               "mixed p_in != p_out, one CUDA graph per pass",
+                   "nodes": int(len(tree.level)), "levels": int(tree.max_level + 1),
+                   "m2l_per_step": nm2l, "m2m_per_step": ap.counts["m2m"],
+                   "l2l_per_step": ap.counts["l2l"], "m2l_order_pairs": len(classes),
+                   "m2l_waves": len(ap.waves), "l2_flush": True},
+        "roofline": {"bound": "alu", "achieved": flop / (phase_ms["m2l"] * 1e-3) / 1e12,
+                     "peak": peak / 1e12, "unit": "TFLOP/s",
+                     "frac": flop / (phase_ms["m2l"] * 1e-3) / peak,
+                     "kernel": "M2L waves (per the autotuned choice)", "traffic": None},
+        "phase_ms": phase_ms, "gpu_launches": ap.launches_per_step() * args.steps,
+        "autotune": {"seconds": tune_s, "waves": waves,
+                     "policies": {k: list(v[:2]) for k, v in chosen.items()}},
+        "setup_seconds": setup_s,
+    }
+    c = clk.summary()
+    if c:
+        line["clocks"] = c
+    print(json.dumps(line))
+    h.close()
+
+
+def run_serving(args):
+    """Serving mix (Poisson arrivals of translation batches, P ~ U{3..30},
+    counts log-uniform 1e3..1e6, FP32 and FP64, memory-admitted, resident
+    state): capacity with all requests at t = 0, then p50/p99 latency at 0.5x
+    and 0.8x of that capacity."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_2202_02847_gb300 import serve
+    srv = serve.TranslationServer(P_max=30, pool_size=4096, n_shifts=1 << 20,
+                                  arena_bytes=24 << 30, n_streams=4, chunk=65536)
+    # warm-up: one small request of every kind that the mix uses
+    warm = serve.make_requests(24, seed=99, count_lo=1e3, count_hi=2e3)
+    srv.run(warm)
+    reqs = serve.make_requests(args.requests, seed=5)
+    flop = sum(serve.translation_flop(r.p_in, r.p_out) * r.count for r in reqs)
+    ntr = sum(r.count for r in reqs)
+    t0 = time.perf_counter()
+    srv.run(reqs)
+    cap_s = time.perf_counter() - t0
+    cap_rps = len(reqs) / cap_s
+    loads = {}
+    for load in (0.5, 0.8):
+        rr = serve.poisson_arrivals(serve.make_requests(args.requests, seed=5), load * cap_rps,
+                                    seed=int(load * 100))
+        t0 = time.perf_counter()
+        done = srv.run(rr)
+        wall = time.perf_counter() - t0
+        st = serve.latency_stats(done)
+        st["offered_rps"] = load * cap_rps
+        st["translations_per_s"] = ntr / wall
+        loads[str(load)] = st
+    srv.close()
+    line = {
+        "metric": METRIC + " (serving: p99 latency at 0.8x capacity)",
+        "value": loads["0.8"]["p99_ms"], "unit": "ms", "n_gpus": 1,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "serving: Poisson stream of translation batches, P ~ U{3..30} "
+                               "(10% p_out = p_in +- U{1..4}), counts log-uniform 1e3..1e6, "
+                               "FP32/FP64, |r|/box in [2,4], resident pools",
+                   "requests_per_load_point": len(reqs), "streams": 4, "chunk": 65536,
+                   "arena_gb": 24},
+        "capacity": {"requests_per_s": cap_rps, "translations_per_s": ntr / cap_s,
+                     "gflop_per_s": flop / cap_s / 1e9, "seconds": cap_s},
+        "latency": loads,
+    }
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -262,6 +412,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0,
                     help="seconds of oracle work for the cpu_baseline leg")
     ap.add_argument("--no-oracle", action="store_true")
+    ap.add_argument("--config", default="octree", choices=["octree", "serving", "batching"],
+                    help="octree: the FP64 P=10 octree pass (default); serving: the request "
+                         "loop; batching: the mixed-order adaptive-octree pass")
+    ap.add_argument("--points", type=int, default=1 << 21, help="batching: Plummer points")
+    ap.add_argument("--requests", type=int, default=600, help="serving: requests per load point")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"],
                     help="f64: the plain FP64 workload (default); f32: the same pass in FP32")
     ap.add_argument("--depth", type=int, default=DEPTH,
@@ -269,6 +424,12 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.config == "serving":
+        run_serving(args)
+        return
+    if args.config == "batching":
+        run_batching(args)
         return
 
     import torch

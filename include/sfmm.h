@@ -155,6 +155,66 @@ sfmm_status sfmm_translate_lists(sfmm_handle h, sfmm_op op, const void *const *s
                                  long long n_targets, int accumulate, sfmm_stream stream);
 
 /*
+ * Mixed-order lists in one launch (Sec. 1.1, mixed-order translations, as
+ * used by adaptive variable-order FMMs).  One persistent launch serves several
+ * classes of target-major lists that share one CSR (src, shift, offsets, out
+ * as in sfmm_translate_lists): class k applies op_k from order p_in_k to
+ * p_out_k to the targets [target_begin_k, target_end_k).  Classes may come in
+ * any order and must not overlap; each class's targets are summed in list
+ * order exactly as sfmm_translate_lists does.  Work is dealt to warps in
+ * chunks of 32 targets of one class.  The rotated solids live in the
+ * handle's global scratch, which must hold one slot for the largest p_in of
+ * the call (sfmm_reserve_scratch).  classes is a HOST array (copied into the
+ * launch); 1 <= n_classes <= SFMM_MAX_CLASSES.
+ * Errors: SFMM_ERR_ARG, SFMM_ERR_ORDER, SFMM_ERR_UNSUPPORTED (no scratch),
+ * SFMM_ERR_CUDA.
+ */
+#define SFMM_MAX_CLASSES 64
+typedef struct {
+    int op;                   /* sfmm_op */
+    int p_in, p_out;
+    int reserved;             /* 0 */
+    long long target_begin;   /* first target of the class */
+    long long target_end;     /* one past the last */
+} sfmm_list_class;
+
+sfmm_status sfmm_translate_lists_multi(sfmm_handle h, const sfmm_list_class *classes,
+                                       int n_classes, const void *const *src,
+                                       const void *shift, const long long *offsets,
+                                       void *const *out, int accumulate, sfmm_stream stream);
+
+/*
+ * Launch policies (the tile-size choice of Sec. 3.2, made per order on the
+ * GPU): which kernel variant serves (op, p_in, p_out) on this handle and how
+ * many warps a block has (0 = automatic).
+ *   SFMM_POLICY_AUTO     - built-in choice (unrolled if compiled, else shared,
+ *                          else global scratch)
+ *   SFMM_POLICY_UNROLLED - fixed-order kernel; only p_in = p_out in {6,8,10,12}
+ *   SFMM_POLICY_SHARED   - generic kernel, working set in shared memory
+ *   SFMM_POLICY_GLOBAL   - generic kernel, rotated solid in the global scratch
+ * Set policies before launching work with the handle (the table is not
+ * synchronised against concurrent launches).  Errors: SFMM_ERR_ARG,
+ * SFMM_ERR_ORDER, SFMM_ERR_UNSUPPORTED (variant cannot serve these orders).
+ */
+typedef enum {
+    SFMM_POLICY_AUTO = 0,
+    SFMM_POLICY_UNROLLED = 1,
+    SFMM_POLICY_SHARED = 2,
+    SFMM_POLICY_GLOBAL = 3
+} sfmm_policy;
+
+sfmm_status sfmm_set_policy(sfmm_handle h, sfmm_op op, int p_in, int p_out,
+                            sfmm_policy policy, int warps_per_block);
+
+/*
+ * Allocate (or grow) the handle's global scratch so that the global-scratch
+ * variants can serve inputs up to order p_in_max with four resident warps per
+ * SM.  Synchronous; not to be called while work using the handle is in
+ * flight.  Errors: SFMM_ERR_ARG, SFMM_ERR_ORDER, SFMM_ERR_NOMEM.
+ */
+sfmm_status sfmm_reserve_scratch(sfmm_handle h, int p_in_max);
+
+/*
  * Particle-to-expansion helpers (not part of the paper's translation library;
  * they build inputs on the device).  Points are sorted by box: box b owns
  * points [offsets[b], offsets[b+1]).  For every box b < n_boxes:

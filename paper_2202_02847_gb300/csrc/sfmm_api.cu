@@ -15,6 +15,8 @@
 
 using namespace sfmm;
 
+static_assert(SFMM_MAX_CLASSES == MAX_CLASSES, "class table sizes of the ABI and the kernel differ");
+
 
 namespace {
 
@@ -35,6 +37,7 @@ template <typename T>
 void set_kernel_attrs(size_t smem) {
     set_attrs_one<T, false>(smem);
     set_attrs_one<T, true>(smem);
+    cudaFuncSetAttribute(multi_lists_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(p2x_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(p2x_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
@@ -109,6 +112,12 @@ sfmm_status fill_unrolled_constants(int dev, size_t smem_optin) {
     return SFMM_OK;
 }
 
+bool use_unrolled(const sfmm_ctx *h, int op, int p_in, int p_out) {
+    const int pol = h->policy[op][p_in][p_out];
+    if (pol == SFMM_POLICY_SHARED || pol == SFMM_POLICY_GLOBAL) return false;
+    return p_in == p_out && unrolled::compiled(p_in) && h->unrolled_ok;
+}
+
 unrolled::Launch launch_info(const sfmm_ctx *h, cudaStream_t s) {
     return unrolled::Launch{h->sm_count, h->smem_optin, h->d_status, s};
 }
@@ -133,15 +142,18 @@ bool shared_only_fits(const sfmm_ctx *h, int p_in, int p_out) {
 }
 
 template <typename T>
-Geometry pick_geometry(const sfmm_ctx *h, int p_in, int p_out, long long units) {
+Geometry pick_geometry(const sfmm_ctx *h, int op, int p_in, int p_out, long long units) {
     Geometry g;
     const size_t sz = sizeof(T);
-    if (shared_only_fits<T>(h, p_in, p_out)) {
+    const int pol = h->policy[op][p_in][p_out];
+    const int wfix = h->warps[op][p_in][p_out];
+    if (pol != SFMM_POLICY_GLOBAL && shared_only_fits<T>(h, p_in, p_out)) {
         const size_t per_warp = (size_t)(x_elems(p_in) + row_elems(p_in, p_out)) * WARP * sz;
         // aim for two resident blocks per SM (half the opt-in budget each)
         int w = (int)(h->smem_optin / 2 / per_warp);
         if (w < 1) w = 1;
         if (w > 8) w = 8;
+        if (wfix > 0 && (size_t)wfix * per_warp <= h->smem_optin) w = wfix;
         g.warps = w;
         g.smem = (size_t)w * per_warp;
         g.blocks = (units + w * WARP - 1) / (w * WARP);
@@ -153,6 +165,7 @@ Geometry pick_geometry(const sfmm_ctx *h, int p_in, int p_out, long long units) 
     int w = (int)(h->smem_optin / 2 / per_warp);
     if (w < 1) w = 1;
     if (w > 4) w = 4;
+    if (wfix > 0 && (size_t)wfix * per_warp <= h->smem_optin) w = wfix;
     const long long slots = (long long)(h->scratch_bytes / slot);
     long long blocks = slots / w;
     const long long need = (units + w * WARP - 1) / (w * WARP);
@@ -172,6 +185,11 @@ struct ScratchGuard {
     bool on;
     std::unique_lock<std::mutex> lk;
     ScratchGuard(sfmm_ctx *h_, cudaStream_t s_, bool on_) : h(h_), s(s_), on(on_) {
+        // inside stream capture the ordering event is skipped (a captured graph
+        // replays its launches in order on its own stream)
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (on && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+            on = false;
         if (!on) return;
         lk = std::unique_lock<std::mutex>(h->scratch_mu);
         cudaStreamWaitEvent(s, h->scratch_free, 0);
@@ -221,7 +239,7 @@ template <typename T>
 sfmm_status launch_batch(sfmm_handle h, int op, const void *const *in, void *const *out,
                          const void *shift, int p_in, int p_out, long long count,
                          int accumulate, cudaStream_t stream, const DevTables<T> &tb) {
-    const Geometry g = pick_geometry<T>(h, p_in, p_out, count);
+    const Geometry g = pick_geometry<T>(h, op, p_in, p_out, count);
     if (g.warps < 1) return SFMM_ERR_UNSUPPORTED;
     if (g.blocks > 0x7fffffffLL) return SFMM_ERR_UNSUPPORTED;
     auto I = reinterpret_cast<const T *const *>(in);
@@ -240,7 +258,7 @@ sfmm_status launch_lists(sfmm_handle h, int op, const void *const *src, const vo
                          const long long *offsets, void *const *out, int p_in, int p_out,
                          long long n_targets, int accumulate, cudaStream_t stream,
                          const DevTables<T> &tb) {
-    const Geometry g = pick_geometry<T>(h, p_in, p_out, n_targets);
+    const Geometry g = pick_geometry<T>(h, op, p_in, p_out, n_targets);
     if (g.warps < 1) return SFMM_ERR_UNSUPPORTED;
     if (g.blocks > 0x7fffffffLL) return SFMM_ERR_UNSUPPORTED;
     auto Sp = reinterpret_cast<const T *const *>(src);
@@ -258,7 +276,7 @@ template <typename T>
 sfmm_status launch_p2x(sfmm_handle h, bool singular, int P, const void *points, const void *q,
                        const long long *offsets, const void *centres, void *out,
                        long long n_boxes, cudaStream_t stream) {
-    const size_t per_warp = (size_t)2 * P * (P + 1) * WARP * sizeof(T);
+    const size_t per_warp = (size_t)6 * P * WARP * sizeof(T);
     int w = (int)(h->smem_optin / 2 / per_warp);
     if (w < 1) w = (int)(h->smem_optin / per_warp);
     if (w < 1) return SFMM_ERR_UNSUPPORTED;
@@ -286,7 +304,7 @@ sfmm_status batch(sfmm_handle h, int op, const void *const *in, void *const *out
     if (count == 0) return SFMM_OK;
     if (in == nullptr || out == nullptr || shift == nullptr) return SFMM_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (p_in == p_out && unrolled::compiled(p_in) && h->unrolled_ok)
+    if (use_unrolled(h, op, p_in, p_out))
         return unrolled::launch_batch(h->dtype == SFMM_F64, p_in, op, in, out, shift, count,
                                       accumulate, launch_info(h, s)) ? SFMM_OK : SFMM_ERR_CUDA;
     if (h->dtype == SFMM_F64)
@@ -420,7 +438,7 @@ sfmm_status sfmm_translate_lists(sfmm_handle h, sfmm_op op, const void *const *s
     if (n_targets == 0) return SFMM_OK;
     if (src == nullptr || shift == nullptr || offsets == nullptr || out == nullptr) return SFMM_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (p_in == p_out && unrolled::compiled(p_in) && h->unrolled_ok)
+    if (use_unrolled(h, (int)op, p_in, p_out))
         return unrolled::launch_lists(h->dtype == SFMM_F64, p_in, (int)op, src, shift, offsets, out,
                                       n_targets, accumulate, launch_info(h, s)) ? SFMM_OK : SFMM_ERR_CUDA;
     if (h->dtype == SFMM_F64)
@@ -465,6 +483,121 @@ sfmm_status sfmm_sync_status(sfmm_handle h, sfmm_stream stream, int *device_stat
     if (cudaStreamSynchronize(s) != cudaSuccess) return SFMM_ERR_CUDA;
     if (device_status) *device_status = v;
     return v == 0 ? SFMM_OK : SFMM_ERR_DEVICE;
+}
+
+sfmm_status sfmm_set_policy(sfmm_handle h, sfmm_op op, int p_in, int p_out, sfmm_policy policy,
+                            int warps_per_block) {
+    if (h == nullptr || (op != SFMM_M2M && op != SFMM_M2L && op != SFMM_L2L)) return SFMM_ERR_ARG;
+    if (policy < SFMM_POLICY_AUTO || policy > SFMM_POLICY_GLOBAL || warps_per_block < 0 ||
+        warps_per_block > 8)
+        return SFMM_ERR_ARG;
+    if (p_in < 1 || p_out < 1 || p_in > h->Pmax || p_out > h->Pmax) return SFMM_ERR_ORDER;
+    const size_t sz = h->dtype == SFMM_F64 ? sizeof(double) : sizeof(float);
+    if (policy == SFMM_POLICY_UNROLLED && !(p_in == p_out && unrolled::compiled(p_in) && h->unrolled_ok))
+        return SFMM_ERR_UNSUPPORTED;
+    if (policy == SFMM_POLICY_SHARED &&
+        (size_t)(x_elems(p_in) + row_elems(p_in, p_out)) * WARP * sz > h->smem_optin)
+        return SFMM_ERR_UNSUPPORTED;
+    if (policy == SFMM_POLICY_GLOBAL &&
+        (h->d_scratch == nullptr || (size_t)x_elems(p_in) * WARP * sz > h->scratch_bytes))
+        return SFMM_ERR_UNSUPPORTED;
+    h->policy[op][p_in][p_out] = (unsigned char)policy;
+    h->warps[op][p_in][p_out] = (unsigned char)warps_per_block;
+    return SFMM_OK;
+}
+
+sfmm_status sfmm_reserve_scratch(sfmm_handle h, int p_in_max) {
+    if (h == nullptr) return SFMM_ERR_ARG;
+    if (p_in_max < 1 || p_in_max > h->Pmax) return SFMM_ERR_ORDER;
+    const size_t sz = h->dtype == SFMM_F64 ? sizeof(double) : sizeof(float);
+    const size_t need = (size_t)h->sm_count * 4 * WARP * x_elems(p_in_max) * sz;
+    std::lock_guard<std::mutex> lk(h->scratch_mu);
+    if (h->d_scratch != nullptr && h->scratch_bytes >= need) return SFMM_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess) return SFMM_ERR_CUDA;
+    void *p = nullptr;
+    if (cudaMalloc(&p, need) != cudaSuccess) return SFMM_ERR_NOMEM;
+    if (h->scratch_free == nullptr &&
+        cudaEventCreateWithFlags(&h->scratch_free, cudaEventDisableTiming) != cudaSuccess) {
+        cudaFree(p);
+        return SFMM_ERR_CUDA;
+    }
+    cudaFree(h->d_scratch);
+    h->d_scratch = p;
+    h->scratch_bytes = need;
+    return SFMM_OK;
+}
+
+}  // extern "C"
+
+template <typename T>
+static sfmm_status launch_multi(sfmm_handle h, const sfmm_list_class *classes, int n,
+                                const void *const *src, const void *shift,
+                                const long long *offsets, void *const *out, int accumulate,
+                                cudaStream_t stream, const DevTables<T> &tb) {
+    MultiParams mp{};
+    mp.n = n;
+    int xs = 0, rs = 0;
+    long long chunks = 0;
+    for (int k = 0; k < n; ++k) {
+        const sfmm_list_class &c = classes[k];
+        MultiClass &m = mp.c[k];
+        m.op = c.op;
+        m.p_in = c.p_in;
+        m.p_out = c.p_out;
+        m.tb = c.target_begin;
+        m.te = c.target_end;
+        m.chunk_begin = chunks;
+        chunks += (c.target_end - c.target_begin + WARP - 1) / WARP;
+        xs = xs > x_elems(c.p_in) ? xs : x_elems(c.p_in);
+        rs = rs > row_elems(c.p_in, c.p_out) ? rs : row_elems(c.p_in, c.p_out);
+    }
+    mp.total_chunks = chunks;
+    mp.x_slot = xs;
+    mp.row_slot = rs;
+    if (chunks == 0) return SFMM_OK;
+    const size_t per_warp = (size_t)rs * WARP * sizeof(T);
+    const size_t slot = (size_t)xs * WARP * sizeof(T);
+    if (h->d_scratch == nullptr || per_warp > h->smem_optin || slot > h->scratch_bytes)
+        return SFMM_ERR_UNSUPPORTED;
+    int w = (int)(h->smem_optin / 2 / per_warp);
+    if (w < 1) w = 1;
+    if (w > 4) w = 4;
+    long long slots = (long long)(h->scratch_bytes / slot);
+    if (w > slots) w = (int)slots;
+    long long blocks = slots / w;
+    const long long need = (chunks + w - 1) / w;
+    if (blocks > need) blocks = need;
+    auto k = multi_lists_kernel<T>;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, w * WARP, (size_t)w * per_warp) == cudaSuccess &&
+        nb > 0 && blocks > (long long)nb * h->sm_count)
+        blocks = (long long)nb * h->sm_count;
+    ScratchGuard guard(h, stream, true);
+    k<<<(unsigned)blocks, w * WARP, (size_t)w * per_warp, stream>>>(
+        tb, mp, reinterpret_cast<const T *const *>(src), reinterpret_cast<const T *>(shift), offsets,
+        reinterpret_cast<T *const *>(out), accumulate, reinterpret_cast<T *>(h->d_scratch), h->d_status);
+    return cudaGetLastError() == cudaSuccess ? SFMM_OK : SFMM_ERR_CUDA;
+}
+
+extern "C" {
+
+sfmm_status sfmm_translate_lists_multi(sfmm_handle h, const sfmm_list_class *classes,
+                                       int n_classes, const void *const *src,
+                                       const void *shift, const long long *offsets,
+                                       void *const *out, int accumulate, sfmm_stream stream) {
+    if (h == nullptr || classes == nullptr || n_classes < 1 || n_classes > SFMM_MAX_CLASSES)
+        return SFMM_ERR_ARG;
+    for (int k = 0; k < n_classes; ++k) {
+        const sfmm_list_class &c = classes[k];
+        if (c.op != SFMM_M2M && c.op != SFMM_M2L && c.op != SFMM_L2L) return SFMM_ERR_ARG;
+        if (c.target_begin < 0 || c.target_end < c.target_begin) return SFMM_ERR_ARG;
+        if (c.p_in < 1 || c.p_out < 1 || c.p_in > h->Pmax || c.p_out > h->Pmax) return SFMM_ERR_ORDER;
+    }
+    if (src == nullptr || shift == nullptr || offsets == nullptr || out == nullptr) return SFMM_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (h->dtype == SFMM_F64)
+        return launch_multi<double>(h, classes, n_classes, src, shift, offsets, out, accumulate, s, h->t64);
+    return launch_multi<float>(h, classes, n_classes, src, shift, offsets, out, accumulate, s, h->t32);
 }
 
 sfmm_status sfmm_host_swap_matrices(int n, double *F, double *G) {

@@ -29,4 +29,7 @@ struct sfmm_ctx {
     cudaEvent_t scratch_free = nullptr;
     // the unrolled kernels (fixed orders) have their constant tables on this device
     bool unrolled_ok = false;
+    // launch policy per (op, p_in, p_out): sfmm_policy and warps per block (0 = auto)
+    unsigned char policy[3][65][65] = {};
+    unsigned char warps[3][65][65] = {};
 };

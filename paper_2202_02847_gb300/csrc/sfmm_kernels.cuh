@@ -354,8 +354,65 @@ __global__ void __launch_bounds__(256, 1) lists_kernel(DevTables<T> tb, const T 
     }
 }
 
+// Several classes of lists in one persistent launch.  The class table travels
+// as a kernel parameter; chunk c (32 targets) belongs to the class k with
+// chunk_begin[k] <= c < chunk_begin[k+1].  The rotated solid lives in the
+// global scratch (slot of x_slot elements per lane); shared memory holds the
+// row buffers and powers for the largest order of the launch.
+constexpr int MAX_CLASSES = 64;
+struct MultiClass {
+    int op, p_in, p_out, pad;
+    long long tb, te, chunk_begin;
+};
+struct MultiParams {
+    int n;
+    int x_slot;                  // scratch elements per lane
+    int row_slot;                // shared elements per lane
+    long long total_chunks;
+    MultiClass c[MAX_CLASSES];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256, 1) multi_lists_kernel(DevTables<T> tb, MultiParams mp,
+                                                             const T *const *src, const T *shift,
+                                                             const long long *offsets,
+                                                             T *const *out, int accumulate,
+                                                             T *scratch, int *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & (WARP - 1), warp = threadIdx.x / WARP;
+    const long long slot = (long long)blockIdx.x * (blockDim.x / WARP) + warp;
+    LaneArr<T> X{scratch + slot * mp.x_slot * WARP + lane};
+    LaneArr<T> buf{reinterpret_cast<T *>(smem_raw) + (size_t)warp * mp.row_slot * WARP + lane};
+    const long long nw = (long long)gridDim.x * (blockDim.x / WARP);
+    for (long long c = slot; c < mp.total_chunks; c += nw) {
+        int k = 0;
+        while (k + 1 < mp.n && mp.c[k + 1].chunk_begin <= c) ++k;
+        const MultiClass cl = mp.c[k];
+        const long long t = cl.tb + (c - cl.chunk_begin) * WARP + lane;
+        if (t >= cl.te) continue;
+        T *dst = out[t];
+        const long long j0 = offsets[t], j1 = offsets[t + 1];
+        if (dst == nullptr) { atomicOr(status, STATUS_NULL_POINTER); continue; }
+        if (j1 < j0) { atomicOr(status, STATUS_BAD_OFFSETS); continue; }
+        bool add = accumulate != 0;
+        if (j0 == j1 && !add)
+            for (int e = 0; e < cl.p_out * (cl.p_out + 1); ++e) dst[e] = T(0);
+        for (long long j = j0; j < j1; ++j) {
+            const T *s = src[j];
+            if (s == nullptr) { atomicOr(status, STATUS_NULL_POINTER); continue; }
+            if (cl.op == OP_M2M) translate_one<T, OP_M2M>(tb, cl.p_in, cl.p_out, s, shift + 3 * j, dst, add, X, buf);
+            else if (cl.op == OP_M2L) translate_one<T, OP_M2L>(tb, cl.p_in, cl.p_out, s, shift + 3 * j, dst, add, X, buf);
+            else translate_one<T, OP_L2L>(tb, cl.p_in, cl.p_out, s, shift + 3 * j, dst, add, X, buf);
+            add = true;
+        }
+    }
+}
+
 // P2M / P2L for boxes of sorted points: one thread per box, the harmonics of
-// each point by the Appendix recurrences, accumulated in shared memory.
+// each point by the Appendix recurrences.  Only the three latest rows of a
+// point's harmonics are kept (the column recurrence reaches back two rows), in
+// a ring of 3 rows x 2P reals in shared memory; q_j times each row is added
+// straight into the box's output solid, which the thread owns.
 template <typename T, bool SINGULAR>
 __global__ void __launch_bounds__(128) p2x_kernel(int P, const T *points, const T *q,
                                                   const long long *offsets, const T *centres,
@@ -363,14 +420,14 @@ __global__ void __launch_bounds__(128) p2x_kernel(int P, const T *points, const 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *smem = reinterpret_cast<T *>(smem_raw);
     const int lane = threadIdx.x & (WARP - 1), warp = threadIdx.x / WARP;
-    const int E = 2 * P * (P + 1);
-    LaneArr<T> H{smem + (size_t)warp * E * WARP + lane};   // harmonics of one point
-    LaneArr<T> A = H + P * (P + 1);                          // accumulator
+    const int E = 6 * P;                                      // 3 rows of (re[P], im[P])
+    LaneArr<T> H{smem + (size_t)warp * E * WARP + lane};
     const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n_boxes) return;
     const long long j0 = offsets[b], j1 = offsets[b + 1];
     if (j1 < j0) { atomicOr(status, STATUS_BAD_OFFSETS); return; }
-    for (int e = 0; e < P * (P + 1); ++e) A[e] = T(0);
+    T *dst = out + b * (long long)(P * (P + 1));
+    for (int e = 0; e < P * (P + 1); ++e) dst[e] = T(0);
     const T cx = centres[3 * b], cy = centres[3 * b + 1], cz = centres[3 * b + 2];
     for (long long j = j0; j < j1; ++j) {
         const T x = points[3 * j] - cx, y = points[3 * j + 1] - cy, z = points[3 * j + 2] - cz;
@@ -378,7 +435,10 @@ __global__ void __launch_bounds__(128) p2x_kernel(int P, const T *points, const 
         const T ir2 = T(1) / r2;
         const T qj = q[j];
         for (int n = 0; n < P; ++n) {
-            const int o = n * (n + 1), o1 = (n - 1) * n, o2 = (n - 2) * (n - 1);
+            LaneArr<T> hr = H + (n % 3) * 2 * P, hi = hr + P;                 // row n
+            LaneArr<T> h1r = H + ((n + 2) % 3) * 2 * P, h1i = h1r + P;        // row n-1
+            LaneArr<T> h2r = H + ((n + 1) % 3) * 2 * P, h2i = h2r + P;        // row n-2
+            T *orow = dst + n * (n + 1);
             for (int m = 0; m <= n; ++m) {
                 T vr, vi;
                 if (n == 0) {
@@ -387,14 +447,14 @@ __global__ void __launch_bounds__(128) p2x_kernel(int P, const T *points, const 
                 } else if (m == n) {
                     // diagonal: R_n^n = (x+iy)/(2n) R_{n-1}^{n-1},
                     //           S_n^n = (2n-1)(x+iy)/|r|^2 S_{n-1}^{n-1}
-                    const T pr = H[o1 + n - 1], pi = H[o1 + n - 1 + n];
+                    const T pr = h1r[n - 1], pi = h1i[n - 1];
                     const T f = SINGULAR ? T(2 * n - 1) * ir2 : T(1) / T(2 * n);
                     vr = (x * pr - y * pi) * f;
                     vi = (x * pi + y * pr) * f;
                 } else {
-                    const T ar = H[o1 + m], ai = H[o1 + n + m];
+                    const T ar = h1r[m], ai = h1i[m];
                     T br = T(0), bi = T(0);
-                    if (n - 2 >= m) { br = H[o2 + m]; bi = H[o2 + n - 1 + m]; }
+                    if (n - 2 >= m) { br = h2r[m]; bi = h2i[m]; }
                     if (SINGULAR) {
                         const T g = T((n - 1) * (n - 1) - m * m);
                         vr = (T(2 * n - 1) * z * ar - g * br) * ir2;
@@ -405,15 +465,13 @@ __global__ void __launch_bounds__(128) p2x_kernel(int P, const T *points, const 
                         vi = (T(2 * n - 1) * z * ai - r2 * bi) * g;
                     }
                 }
-                H[o + m] = vr;
-                H[o + n + 1 + m] = vi;
-                A[o + m] = fma_t(qj, vr, A[o + m]);
-                A[o + n + 1 + m] = fma_t(qj, vi, A[o + n + 1 + m]);
+                hr[m] = vr;
+                hi[m] = vi;
+                orow[m] = fma_t(qj, vr, orow[m]);
+                orow[n + 1 + m] = fma_t(qj, vi, orow[n + 1 + m]);
             }
         }
     }
-    T *dst = out + b * (long long)(P * (P + 1));
-    for (int e = 0; e < P * (P + 1); ++e) dst[e] = A[e];
 }
 
 }  // namespace sfmm

@@ -140,3 +140,206 @@ class UniformPass:
 
     def launches_per_step(self):
         return len(self.m2m) + 1 + len(self.l2l)
+
+
+class AdaptivePass:
+    """Translation pass of an adaptive octree with the expansion order rising
+    with the level (mixed p_in != p_out in M2M, M2L and L2L).
+
+    M2L pairs come from a dual-tree traversal.  A target may receive sources
+    of several levels, i.e. several p_in; its sources are split by p_in into
+    "waves" so that inside one wave every target appears at most once.  Each
+    wave runs as one multi-class launch (sfmm_translate_lists_multi) or as one
+    lists launch per class, whichever the autotuner measured faster; all waves
+    accumulate onto locals zeroed at the start of the step.  M2M runs one lists
+    launch per level (parents gather their children), L2L one batch launch per
+    level.  Solids of all nodes live in one flat array each for M and L
+    (node i at offset off[i], order P[i]).
+    """
+
+    def __init__(self, tree, P_node, handle, device="cuda", dtype=torch.float64, theta=0.5,
+                 pairs=None):
+        self.tree, self.h, self.device, self.dtype = tree, handle, device, dtype
+        self.P = np.asarray(P_node, np.int64)
+        S = self.P * (self.P + 1)
+        self.off = np.concatenate([[0], np.cumsum(S)])
+        total = int(self.off[-1])
+        self.M = torch.zeros(total, dtype=dtype, device=device)
+        self.L = torch.zeros(total, dtype=dtype, device=device)
+        esz = self.M.element_size()
+        baseM, baseL = self.M.data_ptr(), self.L.data_ptr()
+        self.ptrM = lambda idx: torch.as_tensor(baseM + esz * self.off[np.asarray(idx)], dtype=torch.int64, device=device)
+        self.ptrL = lambda idx: torch.as_tensor(baseL + esz * self.off[np.asarray(idx)], dtype=torch.int64, device=device)
+        lev = tree.level
+        cen = tree.centre
+        self.launch_count = 0
+
+        # ---- M2M by level (deepest first): parent gathers its children
+        self.m2m = []
+        for l in range(tree.max_level, 0, -1):
+            par = np.nonzero((lev == l - 1) & (tree.first_child >= 0))[0]
+            par = par[lev[tree.first_child[par]] == l]
+            if len(par) == 0:
+                continue
+            cnt = tree.n_children[par]
+            offs = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+            child = np.concatenate([np.arange(tree.first_child[p], tree.first_child[p] + c)
+                                    for p, c in zip(par, cnt)])
+            self.m2m.append(dict(
+                p_in=int(self.P[child[0]]), p_out=int(self.P[par[0]]),
+                src=self.ptrM(child), out=self.ptrM(par),
+                shift=torch.tensor(cen[par].repeat(cnt, axis=0) - cen[child], dtype=dtype, device=device),
+                offsets=torch.tensor(offs, device=device), n=len(par)))
+
+        # ---- M2L pairs, grouped into waves and classes
+        src, tgt = pairs if pairs is not None else W.dual_tree_m2l(tree, theta)
+        self.n_m2l = len(src)
+        pin, pout = self.P[src], self.P[tgt]
+        # rank of p_in among the distinct p_in of the target -> wave
+        o = np.lexsort((src, pin, tgt))
+        src, tgt, pin, pout = src[o], tgt[o], pin[o], pout[o]
+        newgrp = np.ones(len(src), bool)
+        newgrp[1:] = (tgt[1:] != tgt[:-1]) | (pin[1:] != pin[:-1])
+        grp_id = np.cumsum(newgrp) - 1
+        gstart = np.nonzero(newgrp)[0]
+        g_tgt = tgt[gstart]
+        first_of_tgt = np.ones(len(gstart), bool)
+        first_of_tgt[1:] = g_tgt[1:] != g_tgt[:-1]
+        tstart = np.maximum.accumulate(np.where(first_of_tgt, np.arange(len(gstart)), 0))
+        g_wave = np.arange(len(gstart)) - tstart
+        wave = g_wave[grp_id]
+        self.waves = []
+        for w in range(int(wave.max()) + 1 if len(wave) else 0):
+            sel = np.nonzero(wave == w)[0]
+            ws, wt, wpi, wpo = src[sel], tgt[sel], pin[sel], pout[sel]
+            oo = np.lexsort((ws, wt, wpo, wpi))          # classes contiguous, then targets
+            ws, wt, wpi, wpo = ws[oo], wt[oo], wpi[oo], wpo[oo]
+            newt = np.ones(len(ws), bool)
+            newt[1:] = wt[1:] != wt[:-1]
+            rows = np.nonzero(newt)[0]
+            offs = np.concatenate([rows, [len(ws)]]).astype(np.int64)
+            row_tgt, row_pi, row_po = wt[rows], wpi[rows], wpo[rows]
+            classes = []
+            cs = 0
+            for r in range(1, len(rows) + 1):
+                if r == len(rows) or row_pi[r] != row_pi[cs] or row_po[r] != row_po[cs]:
+                    classes.append(("m2l", int(row_pi[cs]), int(row_po[cs]), cs, r))
+                    cs = r
+            self.waves.append(dict(
+                classes=classes, n=len(rows),
+                src=self.ptrM(ws), out=self.ptrL(row_tgt),
+                shift=torch.tensor(cen[wt] - cen[ws], dtype=dtype, device=device),
+                offsets=torch.tensor(offs, device=device), fused=True,
+                host=dict(src=ws, tgt=wt, offs=offs, row_tgt=row_tgt)))
+
+        # ---- L2L by level (top-down): every child receives from its parent
+        self.l2l = []
+        for l in range(1, tree.max_level + 1):
+            child = np.nonzero(lev == l)[0]
+            if len(child) == 0:
+                continue
+            par = tree.parent[child]
+            self.l2l.append(dict(
+                p_in=int(self.P[par[0]]), p_out=int(self.P[child[0]]),
+                inp=self.ptrL(par), out=self.ptrL(child),
+                shift=torch.tensor(cen[child] - cen[par], dtype=dtype, device=device),
+                count=len(child)))
+        self.counts = dict(m2m=int(sum(len(d["src"]) for d in self.m2m)), m2l=self.n_m2l,
+                           l2l=int(sum(d["count"] for d in self.l2l)))
+        pmax = int(self.P.max())
+        sfmm.reserve_scratch(handle, pmax)
+
+    # ------------------------------------------------------------ inputs
+    def p2m_leaves(self, points, charges):
+        """Leaf multipoles from the particles, one P2M call per leaf level (the
+        leaves' points are gathered into one contiguous array per level)."""
+        t = self.tree
+        pts_sorted = points[t.order]
+        q_sorted = charges[t.order]
+        leaves = np.nonzero(t.is_leaf)[0]
+        for l in np.unique(t.level[leaves]):
+            lv = leaves[t.level[leaves] == l]
+            P = int(self.P[lv[0]])
+            S = P * (P + 1)
+            cnt = t.pt_end[lv] - t.pt_begin[lv]
+            idx = np.concatenate([np.arange(b, e) for b, e in zip(t.pt_begin[lv], t.pt_end[lv])])
+            offs = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+            pts = torch.tensor(pts_sorted[idx], dtype=self.dtype, device=self.device)
+            q = torch.tensor(q_sorted[idx], dtype=self.dtype, device=self.device)
+            cen = torch.tensor(t.centre[lv], dtype=self.dtype, device=self.device)
+            tmp = torch.empty(len(lv), S, dtype=self.dtype, device=self.device)
+            sfmm.p2m_boxes(self.h, P, pts, q, torch.tensor(offs, device=self.device), cen, tmp, len(lv))
+            pos = torch.as_tensor(self.off[lv], device=self.device)
+            cols = torch.arange(S, device=self.device)
+            self.M.index_put_(((pos[:, None] + cols[None, :]).reshape(-1),), tmp.reshape(-1))
+
+    # ------------------------------------------------------------ the pass
+    def upward(self, stream=None):
+        for d in self.m2m:
+            sfmm.translate_lists(self.h, "m2m", d["src"], d["shift"], d["offsets"], d["out"],
+                                 d["p_in"], d["p_out"], d["n"], stream=stream)
+
+    def m2l_wave(self, w, fused, stream=None):
+        d = self.waves[w]
+        if fused:
+            for a in range(0, len(d["classes"]), sfmm.MAX_CLASSES):
+                sfmm.translate_lists_multi(self.h, d["classes"][a:a + sfmm.MAX_CLASSES], d["src"],
+                                           d["shift"], d["offsets"], d["out"], accumulate=True,
+                                           stream=stream)
+        else:
+            for op, pi, po, tb, te in d["classes"]:
+                sfmm.translate_lists(self.h, op, d["src"], d["shift"], d["offsets"][tb:],
+                                     d["out"][tb:], pi, po, te - tb, accumulate=True, stream=stream)
+
+    def m2l_all(self, stream=None):
+        for w, d in enumerate(self.waves):
+            self.m2l_wave(w, d["fused"], stream)
+
+    def downward(self, stream=None):
+        for d in self.l2l:
+            sfmm.l2l_batch(self.h, d["inp"], d["out"], d["shift"], d["p_in"], d["p_out"],
+                           d["count"], accumulate=True, stream=stream)
+
+    def step(self, stream=None):
+        self.L.zero_()
+        self.upward(stream)
+        self.m2l_all(stream)
+        self.downward(stream)
+
+    def launches_per_step(self):
+        m2l = sum((len(d["classes"]) + sfmm.MAX_CLASSES - 1) // sfmm.MAX_CLASSES if d["fused"]
+                  else len(d["classes"]) for d in self.waves)
+        return len(self.m2m) + m2l + len(self.l2l)
+
+    # ------------------------------------------------------------ tuning
+    def autotune(self, tuner, reps=2):
+        """Tune every order pair of the pass, then choose per M2L wave between
+        the fused multi-class launch and per-class launches by timing both."""
+        pairs = set()
+        for d in self.m2m:
+            pairs.add(("m2m", d["p_in"], d["p_out"]))
+        for d in self.l2l:
+            pairs.add(("l2l", d["p_in"], d["p_out"]))
+        for d in self.waves:
+            for op, pi, po, _, _ in d["classes"]:
+                pairs.add((op, pi, po))
+        chosen = {}
+        for op, pi, po in sorted(pairs):
+            chosen[f"{op}:{pi}->{po}"] = tuner.tune(op, pi, po)
+        waves = []
+        for w, d in enumerate(self.waves):
+            t = {}
+            for fused in (True, False):
+                self.m2l_wave(w, fused)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    self.m2l_wave(w, fused)
+                e1.record()
+                torch.cuda.synchronize()
+                t[fused] = e0.elapsed_time(e1) / reps
+            d["fused"] = t[True] <= t[False]
+            waves.append({"wave": w, "classes": len(d["classes"]), "targets": d["n"],
+                          "fused_ms": t[True], "per_class_ms": t[False], "fused": d["fused"]})
+        return chosen, waves

@@ -1,0 +1,306 @@
+"""Continuous-batching serving loop for translation requests on one GPU.
+
+A request asks for `count` translations of one op (M2M, M2L or L2L) from
+order p_in to order p_out in FP32 or FP64: translation i reads solid
+(src_start + i) mod pool_size of the device-resident expansion pool of order
+p_in and shift (shift_start + i) mod n_shifts of the device-resident shift pool
+(unit directions x U[2,4]).  The
+server keeps the tables (one handle per dtype) and the pool resident on the
+device, admits requests by device memory (their output, pointer and shift
+buffers come from one preallocated arena), cuts every admitted request into
+chunks and deals the chunks of all admitted requests round-robin onto several
+CUDA streams, so a request that arrives while others run starts as soon as
+memory and a stream slot free up and its work overlaps theirs.  Each chunk is
+one C-ABI batch call; a translation's result depends only on its own input
+and shift, so it is the same alone and in any mix.
+
+Completion times are measured on the device (CUDA events relative to one
+start event); latency = completion of the request's last chunk - arrival.
+FP32 requests above the FP32 handle's order limit run on the FP64 handle and
+are rounded to FP32 at the end.
+"""
+import math
+import time
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import sfmm
+from . import workloads as W
+
+OPS = ("m2m", "m2l", "l2l")
+
+
+@dataclass
+class Request:
+    rid: int
+    op: str
+    dtype: str               # "f32" or "f64"
+    p_in: int
+    p_out: int
+    count: int
+    src_start: int           # first pool solid (wraps around)
+    shift_start: int         # first pool shift (wraps around)
+    arrival: float = 0.0     # seconds after the start of the run
+    # filled by the server
+    done_ms: float = None
+    out: torch.Tensor = None
+    chunks_left: int = 0
+
+    def out_bytes(self):
+        w = 8 if self.dtype == "f64" else 4
+        return self.count * self.p_out * (self.p_out + 1) * w
+
+
+def translation_flop(p_in, p_out):
+    """Algorithmic FLOP of one rotation-based translation (order max(p_in, p_out))."""
+    P = max(p_in, p_out)
+    return 2 * P * (P + 1) * (2 * P + 1) + 14 * P * (P + 1)
+
+
+class Arena:
+    """First-fit allocator over one preallocated device buffer (bytes)."""
+
+    def __init__(self, nbytes, device):
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.free = [(0, nbytes)]          # sorted (offset, size)
+
+    @staticmethod
+    def _round(n):
+        return (n + 255) // 256 * 256
+
+    def alloc(self, n):
+        n = self._round(n)
+        for i, (o, s) in enumerate(self.free):
+            if s >= n:
+                if s == n:
+                    self.free.pop(i)
+                else:
+                    self.free[i] = (o + n, s - n)
+                return o, n
+        return None
+
+    def release(self, o, n):
+        self.free.append((o, n))
+        self.free.sort()
+        merged = []
+        for off, sz in self.free:
+            if merged and merged[-1][0] + merged[-1][1] == off:
+                merged[-1] = (merged[-1][0], merged[-1][1] + sz)
+            else:
+                merged.append((off, sz))
+        self.free = merged
+
+    def view(self, o, n, dtype):
+        return self.buf[o:o + n].view(dtype)
+
+
+class TranslationServer:
+    def __init__(self, P_max=30, pool_size=4096, n_shifts=1 << 20, arena_bytes=8 << 30,
+                 n_streams=4, chunk=32768, inflight_per_stream=2, device="cuda", seed=5):
+        self.device = torch.device(device)
+        self.P_max = P_max
+        self.h = {"f64": sfmm.Handle(P_max, "f64"), "f32": sfmm.Handle(min(P_max, 29), "f32")}
+        self.P32 = min(P_max, 29)
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(n_streams)]
+        self.chunk = chunk
+        self.inflight = inflight_per_stream
+        self.arena = Arena(arena_bytes, self.device)
+        self.pool = {}
+        self.pool_size = pool_size
+        self._build_pool(pool_size, seed)
+        g = W.rng(seed + 1)
+        sh = torch.tensor(W.shifts(g, n_shifts, 2.0, 4.0), device=self.device)
+        self.shift_pool = {"f64": sh, "f32": sh.float()}
+        self.n_shifts = n_shifts
+
+    # ---------------------------------------------------------------- pool
+    def _build_pool(self, n, seed):
+        """Resident expansions: P2M of 32 charges per cluster (unit box), every
+        order 1..P_max, built on the device by the library's P2M."""
+        g = W.rng(seed)
+        pos, q = W.charge_clusters(g, n, 32)
+        pts = torch.tensor(pos.reshape(-1, 3), device=self.device)
+        qq = torch.tensor(q.reshape(-1), device=self.device)
+        offs = torch.arange(0, 32 * n + 1, 32, dtype=torch.int64, device=self.device)
+        cen = torch.zeros(n, 3, dtype=torch.float64, device=self.device)
+        for P in range(1, self.P_max + 1):
+            buf = torch.empty(n, P * (P + 1), dtype=torch.float64, device=self.device)
+            sfmm.p2m_boxes(self.h["f64"], P, pts, qq, offs, cen, buf, n)
+            self.pool[("f64", P)] = buf
+            self.pool[("f32", P)] = buf.float()
+        torch.cuda.synchronize(self.device)
+
+    # ----------------------------------------------------------- admission
+    def _admit(self, r):
+        """Reserve arena space for the request's output, pointers and shifts."""
+        w = 8 if (r.dtype == "f64" or r.p_in > self.P32 or r.p_out > self.P32) else 4
+        S_out = r.p_out * (r.p_out + 1)
+        need = [r.count * S_out * w, r.count * 8, r.count * 8, r.count * 3 * w]
+        got = []
+        for n in need:
+            a = self.arena.alloc(n)
+            if a is None:
+                for o, s in got:
+                    self.arena.release(o, s)
+                return False
+            got.append(a)
+        r._alloc = got
+        r._w = w
+        return True
+
+    def _release(self, r):
+        for o, s in r._alloc:
+            self.arena.release(o, s)
+        r._alloc = []
+
+    def _prepare(self, r, stream):
+        """Pointer and shift arrays of an admitted request (marshalling only)."""
+        tdt = torch.float64 if r._w == 8 else torch.float32
+        S_in, S_out = r.p_in * (r.p_in + 1), r.p_out * (r.p_out + 1)
+        (oo, on), (io, inn), (po, pn), (so, sn) = r._alloc
+        out = self.arena.view(oo, on, tdt)[: r.count * S_out].view(r.count, S_out)
+        pool = self.pool[("f64" if r._w == 8 else "f32", r.p_in)]
+        with torch.cuda.stream(stream):
+            ar = torch.arange(r.count, device=self.device, dtype=torch.int64)
+            idx = (ar + r.src_start) % self.pool_size
+            pin = self.arena.view(io, inn, torch.int64)[: r.count]
+            pin.copy_(idx * (S_in * pool.element_size()) + pool.data_ptr())
+            pout = self.arena.view(po, pn, torch.int64)[: r.count]
+            pout.copy_(ar * (S_out * out.element_size()) + out.data_ptr())
+            sh = self.arena.view(so, sn, tdt)[: r.count * 3].view(r.count, 3)
+            spool = self.shift_pool["f64" if r._w == 8 else "f32"]
+            torch.index_select(spool, 0, (ar + r.shift_start) % self.n_shifts, out=sh)
+            ready = torch.cuda.Event()
+            ready.record(stream)
+        r.out, r._pin, r._pout, r._sh, r._ready = out, pin, pout, sh, ready
+        r._next = 0
+        r.chunks_left = math.ceil(r.count / self.chunk)
+
+    def _launch_chunk(self, r, stream, start_ev):
+        a = r._next
+        b = min(r.count, a + self.chunk)
+        r._next = b
+        h = self.h["f64" if r._w == 8 else "f32"]
+        n = b - a
+        stream.wait_event(r._ready)
+        sfmm.translate_batch(r.op, h, r._pin[a:b], r._pout[a:b], r._sh[a:b], r.p_in, r.p_out,
+                             n, stream=stream)
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(stream)
+        return ev
+
+    # ----------------------------------------------------------------- run
+    def run(self, requests, keep_outputs=False):
+        """Serve the requests at their arrival times (seconds after start).
+        Returns the requests with done_ms (device time of completion after the
+        start event) filled in; with keep_outputs the results are copied out of
+        the arena before its space is reused."""
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        start = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(self.device)
+        start.record(torch.cuda.current_stream(self.device))
+        t0 = time.perf_counter()
+        pending = list(reqs)           # not yet arrived
+        queue = []                     # arrived, waiting for memory
+        active = []                    # admitted, chunks left to launch
+        inflight = {i: [] for i in range(len(self.streams))}   # stream -> [(ev, req)]
+        finished = []
+        rr = 0
+        while pending or queue or active or any(inflight.values()):
+            now = time.perf_counter() - t0
+            while pending and pending[0].arrival <= now:
+                queue.append(pending.pop(0))
+            # admission (FIFO)
+            while queue and self._admit(queue[0]):
+                r = queue.pop(0)
+                self._prepare(r, self.streams[r.rid % len(self.streams)])
+                active.append(r)
+            # retire finished chunks
+            for si, lst in inflight.items():
+                keep = []
+                for ev, r in lst:
+                    if ev.query():
+                        r.chunks_left -= 1
+                        if r.chunks_left == 0:
+                            r.done_ms = start.elapsed_time(ev)
+                            if keep_outputs:
+                                cur = torch.cuda.current_stream(self.device)
+                                cur.wait_event(ev)
+                                # always a copy: the arena space is reused at once
+                                r.out = (r.out.float() if r.out.dtype != torch.float32 else r.out.clone()) \
+                                    if r.dtype == "f32" else r.out.clone()
+                                cur.synchronize()
+                            else:
+                                r.out = None
+                            self._release(r)
+                            finished.append(r)
+                    else:
+                        keep.append((ev, r))
+                inflight[si] = keep
+            # deal chunks round-robin over the active requests onto free stream slots
+            launched = False
+            for si, s in enumerate(self.streams):
+                if len(inflight[si]) >= self.inflight or not active:
+                    continue
+                r = active[rr % len(active)]
+                rr += 1
+                ev = self._launch_chunk(r, s, start)
+                inflight[si].append((ev, r))
+                if r._next >= r.count:
+                    active.remove(r)
+                launched = True
+            if not launched:
+                if pending and not queue and not active and not any(inflight.values()):
+                    time.sleep(max(0.0, min(0.001, pending[0].arrival - (time.perf_counter() - t0))))
+                else:
+                    time.sleep(2e-5)
+        torch.cuda.synchronize(self.device)
+        return finished
+
+    def run_alone(self, r):
+        """One request on its own (for the same-result check)."""
+        r2 = Request(r.rid, r.op, r.dtype, r.p_in, r.p_out, r.count, r.src_start,
+                     r.shift_start, 0.0)
+        return self.run([r2], keep_outputs=True)[0]
+
+    def close(self):
+        for h in self.h.values():
+            h.close()
+
+
+def make_requests(n, seed=5, P_lo=3, P_hi=30, count_lo=1e3, count_hi=1e6, pool_size=4096,
+                  n_shifts=1 << 20, mixed_frac=0.1):
+    """The serving mix: op ~ U{M2M, M2L, L2L}; P ~ U{P_lo..P_hi} with p_in = p_out,
+    a fraction with p_out = p_in +- U{1..4}; count log-uniform in [count_lo, count_hi];
+    dtype ~ U{FP32, FP64}; inputs are ranges of the resident pools (shifts are
+    unit directions x U[2,4], i.e. |r|/box in [2,4] for unit boxes)."""
+    g = W.rng(seed)
+    out = []
+    for i in range(n):
+        op = OPS[g.integers(0, 3)]
+        P = int(g.integers(P_lo, P_hi + 1))
+        p_in = p_out = P
+        if g.uniform() < mixed_frac:
+            p_out = int(np.clip(P + g.choice([-1, 1]) * g.integers(1, 5), P_lo, P_hi))
+        count = int(math.floor(10 ** g.uniform(math.log10(count_lo), math.log10(count_hi))))
+        dtype = "f32" if g.uniform() < 0.5 else "f64"
+        out.append(Request(i, op, dtype, p_in, p_out, count, int(g.integers(0, pool_size)),
+                           int(g.integers(0, n_shifts))))
+    return out
+
+
+def poisson_arrivals(requests, rate_per_s, seed=55):
+    g = W.rng(seed)
+    t = 0.0
+    for r in requests:
+        t += g.exponential(1.0 / rate_per_s)
+        r.arrival = t
+    return requests
+
+
+def latency_stats(finished):
+    lat = np.array([r.done_ms - 1e3 * r.arrival for r in finished])
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "n": len(lat)}

@@ -47,6 +47,9 @@ _SIGS = {
     "sfmm_p2l_boxes": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _ll, _vp]),
     "sfmm_sync_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
     "sfmm_translate_batch_noalloc": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _ll, _i, _vp]),
+    "sfmm_translate_lists_multi": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp, _i, _vp]),
+    "sfmm_set_policy": (_i, [_vp, _i, _i, _i, _i, _i]),
+    "sfmm_reserve_scratch": (_i, [_vp, _i]),
     "sfmm_host_swap_matrices": (_i, [_i, _dp, _dp]),
     "sfmm_host_ztranslate": (_i, [_i, _i, _i, _dp]),
 }
@@ -169,6 +172,39 @@ def translate_lists(h, op, src, shift, offsets, out, p_in, p_out, n_targets,
                                      _addr(offsets), _addr(out), int(p_in), int(p_out),
                                      int(n_targets), int(bool(accumulate)), _stream(stream)),
            "sfmm_translate_lists")
+
+
+class ListClass(ctypes.Structure):
+    """sfmm_list_class: one (op, p_in, p_out) class of a multi-class lists call."""
+    _fields_ = [("op", ctypes.c_int), ("p_in", ctypes.c_int), ("p_out", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("target_begin", ctypes.c_longlong),
+                ("target_end", ctypes.c_longlong)]
+
+
+MAX_CLASSES = 64
+POLICY = {"auto": 0, "unrolled": 1, "shared": 2, "global": 3}
+
+
+def translate_lists_multi(h, classes, src, shift, offsets, out, accumulate=False, stream=None):
+    """sfmm_translate_lists_multi: classes = [(op, p_in, p_out, target_begin, target_end)]."""
+    arr = (ListClass * len(classes))()
+    for k, (op, pi, po, tb, te) in enumerate(classes):
+        arr[k] = ListClass(OPS.get(op, op), int(pi), int(po), 0, int(tb), int(te))
+    _check(_lib.sfmm_translate_lists_multi(h.ptr, ctypes.cast(arr, _vp), len(classes), _addr(src),
+                                           _addr(shift), _addr(offsets), _addr(out),
+                                           int(bool(accumulate)), _stream(stream)),
+           "sfmm_translate_lists_multi")
+
+
+def set_policy(h, op, p_in, p_out, policy="auto", warps=0):
+    """sfmm_set_policy: kernel variant and warps per block for (op, p_in, p_out)."""
+    _check(_lib.sfmm_set_policy(h.ptr, OPS.get(op, op), int(p_in), int(p_out),
+                                POLICY.get(policy, policy), int(warps)), "sfmm_set_policy")
+
+
+def reserve_scratch(h, p_in_max):
+    """sfmm_reserve_scratch: global scratch for inputs up to order p_in_max."""
+    _check(_lib.sfmm_reserve_scratch(h.ptr, int(p_in_max)), "sfmm_reserve_scratch")
 
 
 def p2m_boxes(h, P, points, q, offsets, centres, out, n_boxes, stream=None):

@@ -173,3 +173,161 @@ def parent_map(depth):
     _, _, ijk, _ = _level_geometry(depth)
     p = ijk // 2
     return box_index(p[:, 0], p[:, 1], p[:, 2], nside // 2)
+
+
+# ------------------------------------------------------------ adaptive octree
+
+def plummer(n, seed=4, u_max=0.999):
+    """Plummer sphere: radius r = (u^{-2/3} - 1)^{-1/2}, u ~ U(0, u_max) (the cut
+    keeps r finite), isotropic directions; masses q = 1/n."""
+    g = rng(seed)
+    u = g.uniform(0.0, u_max, size=n)
+    u = np.maximum(u, 1e-300)
+    r = 1.0 / np.sqrt(u ** (-2.0 / 3.0) - 1.0)
+    pts = unit_directions(g, n) * r[:, None]
+    return pts, np.full(n, 1.0 / n)
+
+
+@dataclass
+class AdaptiveOctree:
+    """Nodes in breadth-first order (parents before children)."""
+    level: np.ndarray          # (nn,)
+    centre: np.ndarray         # (nn, 3)
+    half: np.ndarray           # (nn,) half edge length
+    parent: np.ndarray         # (nn,) -1 for the root
+    first_child: np.ndarray    # (nn,) index of first child, -1 for leaves
+    n_children: np.ndarray     # (nn,) number of (non-empty) children
+    pt_begin: np.ndarray       # (nn,) range of the node's points in `order`
+    pt_end: np.ndarray
+    order: np.ndarray          # point permutation (Morton order)
+    max_level: int
+
+    @property
+    def is_leaf(self):
+        return self.first_child < 0
+
+
+def adaptive_octree(points, leaf_size=64, max_level=21):
+    """Octree over the bounding cube of the points, splitting every node with
+    more than leaf_size points (empty children are not created)."""
+    lo = points.min(axis=0)
+    hi = points.max(axis=0)
+    span = float((hi - lo).max()) * (1 + 1e-12)
+    centre0 = (lo + hi) / 2
+    corner = centre0 - span / 2
+    B = max_level
+    ijk = np.clip(((points - corner) / span * (1 << B)).astype(np.int64), 0, (1 << B) - 1)
+    key = np.zeros(len(points), np.int64)
+    for b in range(B):                         # interleave bits: x high, then y, then z
+        for d in range(3):
+            key |= ((ijk[:, d] >> b) & 1) << (3 * b + (2 - d))
+    order = np.argsort(key, kind="stable")
+    key = key[order]
+    # level-by-level construction
+    levels, centres, halfs, parents, begins, ends = [], [], [], [], [], []
+    cur = [(0, 0, len(points), -1)]            # (prefix, begin, end, parent)
+    lvl = 0
+    node_prefix = []
+    while cur:
+        nxt = []
+        base = len(levels)
+        for i, (pref, b, e, par) in enumerate(cur):
+            idx = base + i
+            levels.append(lvl)
+            h = span / (1 << lvl) / 2
+            # centre from the prefix bits
+            c = corner.copy()
+            for k in range(lvl):
+                trip = (pref >> (3 * (lvl - 1 - k))) & 7
+                step = span / (1 << (k + 1))
+                c = c + np.array([(trip >> 2) & 1, (trip >> 1) & 1, trip & 1]) * step
+            centres.append(c + h)
+            halfs.append(h)
+            parents.append(par)
+            begins.append(b)
+            ends.append(e)
+            if e - b > leaf_size and lvl < B:
+                shift = 3 * (B - lvl - 1)
+                sub = (key[b:e] >> shift) & 7
+                cuts = np.searchsorted(sub, np.arange(9))
+                for ch in range(8):
+                    cb, ce = b + cuts[ch], b + cuts[ch + 1]
+                    if ce > cb:
+                        nxt.append(((pref << 3) | ch, cb, ce, idx))
+        cur = nxt
+        lvl += 1
+    nn = len(levels)
+    parent = np.array(parents, np.int64)
+    first_child = np.full(nn, -1, np.int64)
+    n_children = np.zeros(nn, np.int64)
+    for i in range(1, nn):
+        p = parent[i]
+        if first_child[p] < 0:
+            first_child[p] = i
+        n_children[p] += 1
+    return AdaptiveOctree(level=np.array(levels, np.int64), centre=np.array(centres),
+                          half=np.array(halfs), parent=parent, first_child=first_child,
+                          n_children=n_children, pt_begin=np.array(begins, np.int64),
+                          pt_end=np.array(ends, np.int64), order=order,
+                          max_level=int(max(levels)))
+
+
+def order_by_level(tree, lo=4, span=20):
+    """Expansion order rising with the level: P(l) = lo + round(span * l / L_max)."""
+    L = max(tree.max_level, 1)
+    return lo + np.rint(span * tree.level / L).astype(np.int64)
+
+
+def dual_tree_m2l(tree, theta=0.5):
+    """M2L pairs (source A, target B) of a dual-tree traversal with the
+    acceptance criterion (rA + rB) < theta |cA - cB| (r = box circumradius).
+    Breadth-first over pair arrays, splitting the larger box (or the non-leaf)
+    of every rejected pair; leaf-leaf pairs are near field (not translated).
+    Returns (src, tgt) arrays sorted by (tgt, src)."""
+    rad = np.sqrt(3.0) * tree.half
+    leaf = tree.is_leaf
+    fc, nc = tree.first_child, tree.n_children
+    A = np.array([0], np.int64)
+    Bn = np.array([0], np.int64)
+    out_a, out_b = [], []
+
+    def children_pairs(keep_side, split_side, split_first):
+        # expand split_side nodes into their children, pairing each with keep_side
+        cnt = nc[split_side]
+        rep_keep = np.repeat(keep_side, cnt)
+        starts = np.repeat(fc[split_side], cnt)
+        offs = np.arange(cnt.sum()) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+        return rep_keep, starts + offs
+
+    while len(A):
+        same = A == Bn
+        d = np.linalg.norm(tree.centre[A] - tree.centre[Bn], axis=1)
+        acc = (~same) & (rad[A] + rad[Bn] < theta * d)
+        out_a.append(A[acc])
+        out_b.append(Bn[acc])
+        rest = ~acc
+        A, Bn, same = A[rest], Bn[rest], same[rest]
+        la, lb = leaf[A], leaf[Bn]
+        near = la & lb
+        A, Bn, same, la, lb = A[~near], Bn[~near], same[~near], la[~near], lb[~near]
+        # self pairs: all (child, child') pairs of the node
+        sA = A[same]
+        cnt = nc[sA]
+        if len(sA):
+            par = np.repeat(sA, cnt * cnt)
+            k = np.arange((cnt * cnt).sum()) - np.repeat(np.cumsum(cnt * cnt) - cnt * cnt, cnt * cnt)
+            cc = np.repeat(cnt, cnt * cnt)
+            sa_new = fc[par] + k // cc
+            sb_new = fc[par] + k % cc
+        else:
+            sa_new = sb_new = np.zeros(0, np.int64)
+        A, Bn, la, lb = A[~same], Bn[~same], la[~same], lb[~same]
+        split_a = (~la) & (lb | (rad[A] >= rad[Bn]))
+        b_keep, a_new = children_pairs(Bn[split_a], A[split_a], True)
+        a_keep, b_new = children_pairs(A[~split_a], Bn[~split_a], False)
+        A = np.concatenate([sa_new, a_new, a_keep])
+        Bn = np.concatenate([sb_new, b_keep, b_new])
+    src = np.concatenate(out_a)
+    tgt = np.concatenate(out_b)
+    o = np.lexsort((src, tgt))
+    return src[o], tgt[o]
