@@ -215,6 +215,33 @@ sfmm_status sfmm_set_policy(sfmm_handle h, sfmm_op op, int p_in, int p_out,
 sfmm_status sfmm_reserve_scratch(sfmm_handle h, int p_in_max);
 
 /*
+ * Shift-grouped M2L on one level of a uniform octree, on the tensor cores.
+ * The paper notes that with a finite set of shift vectors the translation
+ * matrices can be stored and applied to many solids at once as BLAS
+ * matrix-matrix products (Sec. 2.2).  On a uniform level the M2L shifts of the
+ * standard interaction list are the 316 integer offsets u (box units,
+ * max|u_i| in {2,3}); for P = 16 each has one real 256x256 matrix in the
+ * box-scaled orthonormal basis, built once (in FP64, with this library's
+ * rotation-based M2L applied to the basis vectors) by sfmm_grid_create, which
+ * also allocates the workspaces (synchronous).
+ * sfmm_grid_m2l: L (+)= M2L of every box's interaction list on an nside^3 grid
+ * (nside a multiple of 8, box i at (ix*nside + iy)*nside + iz, solids of order
+ * 16 stored contiguously, FP64 device arrays M and L).  Products run in
+ * 3xTF32 (hi*hi + hi*lo + lo*hi, about 21 bits) with FP32 accumulation over 8
+ * offsets and FP64 accumulation per target; results agree with the FP64
+ * rotation path to about 1e-6 (weighted coefficient error).  Asynchronous on
+ * `stream`; one call at a time per grid object.  A device-side wait that gives
+ * up sets bit 4 of the handle's status word (sfmm_sync_status).
+ * Errors: SFMM_ERR_ARG, SFMM_ERR_ORDER (handle not FP64 or P_max < 16),
+ * SFMM_ERR_UNSUPPORTED (P != 16), SFMM_ERR_NOMEM, SFMM_ERR_CUDA.
+ */
+typedef struct sfmm_grid_ctx *sfmm_grid;
+sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out);
+sfmm_status sfmm_grid_m2l(sfmm_grid g, double box_size, const void *M, void *L, int accumulate,
+                          sfmm_stream stream);
+sfmm_status sfmm_grid_destroy(sfmm_grid g);
+
+/*
  * Particle-to-expansion helpers (not part of the paper's translation library;
  * they build inputs on the device).  Points are sorted by box: box b owns
  * points [offsets[b], offsets[b+1]).  For every box b < n_boxes:

@@ -50,6 +50,9 @@ _SIGS = {
     "sfmm_translate_lists_multi": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp, _i, _vp]),
     "sfmm_set_policy": (_i, [_vp, _i, _i, _i, _i, _i]),
     "sfmm_reserve_scratch": (_i, [_vp, _i]),
+    "sfmm_grid_create": (_i, [_vp, _i, _i, ctypes.POINTER(_vp)]),
+    "sfmm_grid_m2l": (_i, [_vp, ctypes.c_double, _vp, _vp, _i, _vp]),
+    "sfmm_grid_destroy": (_i, [_vp]),
     "sfmm_host_swap_matrices": (_i, [_i, _dp, _dp]),
     "sfmm_host_ztranslate": (_i, [_i, _i, _i, _dp]),
 }
@@ -205,6 +208,31 @@ def set_policy(h, op, p_in, p_out, policy="auto", warps=0):
 def reserve_scratch(h, p_in_max):
     """sfmm_reserve_scratch: global scratch for inputs up to order p_in_max."""
     _check(_lib.sfmm_reserve_scratch(h.ptr, int(p_in_max)), "sfmm_reserve_scratch")
+
+
+class Grid:
+    """sfmm_grid_create / sfmm_grid_m2l / sfmm_grid_destroy: tensor-core M2L of one
+    uniform octree level (P = 16)."""
+
+    def __init__(self, h, P, nside):
+        g = _vp()
+        _check(_lib.sfmm_grid_create(h.ptr, int(P), int(nside), ctypes.byref(g)), "sfmm_grid_create")
+        self._g, self.P, self.nside = g, P, nside
+
+    def m2l(self, box_size, M, L, accumulate=False, stream=None):
+        _check(_lib.sfmm_grid_m2l(self._g, float(box_size), _addr(M), _addr(L),
+                                  int(bool(accumulate)), _stream(stream)), "sfmm_grid_m2l")
+
+    def close(self):
+        if getattr(self, "_g", None):
+            _lib.sfmm_grid_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def p2m_boxes(h, P, points, q, offsets, centres, out, n_boxes, stream=None):

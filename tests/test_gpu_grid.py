@@ -1,0 +1,84 @@
+"""Tensor-core shift-grouped M2L on a uniform octree level (P = 16) against
+the FP64 rotation path on the same interaction lists and against the oracle."""
+import numpy as np
+import pytest
+
+from paper_2202_02847_gb300 import workloads as W
+import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+P = 16
+TOL = 1e-5     # FP32-class: 3xTF32 products, FP64 target sums
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_2202_02847_gb300 import sfmm
+    h = sfmm.Handle(P, "f64")
+    yield sfmm, h
+    h.close()
+
+
+@pytest.mark.parametrize("depth", [3, 4])
+def test_grid_m2l_matches_rotation_path_and_oracle(env, orc, depth):
+    import torch
+    sfmm, h = env
+    ns = 1 << depth
+    tree = W.uniform_octree(depth)
+    lv = tree.levels[depth]
+    g = W.rng(300 + depth)
+    # multipoles of a level from P2M of 16 random charges per box (on the device)
+    nb = ns ** 3
+    pos = lv.centres[:, None, :] + g.uniform(-0.5, 0.5, size=(nb, 16, 3)) * lv.h
+    q = g.uniform(-1, 1, size=(nb, 16))
+    M = torch.zeros(nb, P * (P + 1), dtype=torch.float64, device="cuda")
+    sfmm.p2m_boxes(h, P, torch.tensor(pos.reshape(-1, 3), device="cuda"),
+                   torch.tensor(q.reshape(-1), device="cuda"),
+                   torch.arange(0, 16 * nb + 1, 16, dtype=torch.int64, device="cuda"),
+                   torch.tensor(lv.centres, device="cuda"), M, nb)
+    grid = sfmm.Grid(h, P, ns)
+    Lg = torch.zeros_like(M)
+    grid.m2l(lv.h, M, Lg)
+    # the FP64 rotation path on the same lists
+    Lr = torch.zeros_like(M)
+    S = P * (P + 1)
+    src = sfmm.pointer_array(M, S, torch.as_tensor(lv.m2l_sources))
+    out = sfmm.pointer_array(Lr, S, torch.arange(nb))
+    sfmm.translate_lists(h, "m2l", src, torch.tensor(lv.m2l_shift, device="cuda"),
+                         torch.tensor(lv.m2l_offsets, device="cuda"), out, P, P, nb)
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    a, b = Lg.cpu().numpy(), Lr.cpu().numpy()
+    err = U.rel_err(a, b, P, "L")
+    assert err <= TOL, err
+    # accumulate mode adds
+    grid.m2l(lv.h, M, Lg, accumulate=True)
+    torch.cuda.synchronize()
+    assert U.rel_err(Lg.cpu().numpy(), 2 * b, P, "L") <= TOL
+    # a few targets against the oracle (its own multipoles from the charges)
+    Mh = M.cpu().numpy()
+    for t in g.choice(nb, size=3, replace=False):
+        j0, j1 = lv.m2l_offsets[t], lv.m2l_offsets[t + 1]
+        want = np.zeros(S)
+        for j in range(j0, j1):
+            s = lv.m2l_sources[j]
+            Ms = orc.p2m(P, pos[s], q[s], lv.centres[s])
+            want += orc.translate("m2l", P, P, Ms, lv.m2l_shift[j])
+        assert U.rel_err(a[t], want, P, "L") <= TOL
+    grid.close()
+
+
+def test_grid_rejects_bad_arguments(env):
+    sfmm, h = env
+    with pytest.raises(sfmm.SfmmError) as e:
+        sfmm.Grid(h, 12, 16)
+    assert e.value.code == 6
+    with pytest.raises(sfmm.SfmmError) as e:
+        sfmm.Grid(h, 16, 12)
+    assert e.value.code == 1
