@@ -253,6 +253,107 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_precision(args):
+    """Precision workload: level 5 of the uniform octree (32^3 boxes, 1M points,
+    seed 3) at P = 16.  The level's 5,398,920 M2L run three ways on the same
+    multipoles: shift-grouped on the tensor cores (3xTF32, FP64 target sums),
+    rotation-based in FP64, rotation-based in FP32; errors are stated against
+    the FP64 rotation path (itself checked against the oracle on sampled
+    targets by the test suite)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_2202_02847_gb300 import sfmm, workloads as W
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import gpu_util as U
+    Pp, depth = 16, 5
+    tree = W.uniform_octree(depth, NPOINTS, seed=3)
+    lv = tree.levels[depth]
+    nb = 8 ** depth
+    S = Pp * (Pp + 1)
+    h64, h32 = sfmm.Handle(Pp, "f64"), sfmm.Handle(Pp, "f32")
+    order = np.argsort(tree.leaf_of_point, kind="stable")
+    cnt = np.bincount(tree.leaf_of_point, minlength=nb)
+    offs = torch.tensor(np.concatenate([[0], np.cumsum(cnt)]), device="cuda")
+    M = torch.zeros(nb, S, dtype=torch.float64, device="cuda")
+    sfmm.p2m_boxes(h64, Pp, torch.tensor(tree.points[order], device="cuda"),
+                   torch.tensor(tree.charges[order], device="cuda"), offs,
+                   torch.tensor(lv.centres, device="cuda"), M, nb)
+    M32 = M.float()
+    grid = sfmm.Grid(h64, Pp, 1 << depth)
+    L_tc = torch.zeros_like(M)
+    L64 = torch.zeros_like(M)
+    L32 = torch.zeros_like(M32)
+    src64 = sfmm.pointer_array(M, S, torch.as_tensor(lv.m2l_sources))
+    src32 = sfmm.pointer_array(M32, S, torch.as_tensor(lv.m2l_sources))
+    out64 = sfmm.pointer_array(L64, S, torch.arange(nb))
+    out32 = sfmm.pointer_array(L32, S, torch.arange(nb))
+    sh64 = torch.tensor(lv.m2l_shift, device="cuda")
+    sh32 = sh64.float()
+    loffs = torch.tensor(lv.m2l_offsets, device="cuda")
+    runs = {
+        "tensor_3xtf32": lambda: grid.m2l(lv.h, M, L_tc),
+        "rotation_fp64": lambda: sfmm.translate_lists(h64, "m2l", src64, sh64, loffs, out64, Pp, Pp, nb),
+        "rotation_fp32": lambda: sfmm.translate_lists(h32, "m2l", src32, sh32, loffs, out32, Pp, Pp, nb),
+    }
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    times = {}
+    with ClockSampler(0) as clk:
+        for name, f in runs.items():
+            reps = max(1, args.steps) if name != "rotation_fp64" else 1
+            for _ in range(max(1, args.warmup if name != "rotation_fp64" else 1)):
+                f()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(reps):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                f()
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            times[name] = float(np.median(ms))
+    assert h64.sync_status() == 0 and h32.sync_status() == 0
+    ref = L64.cpu().numpy()
+    err = {"tensor_3xtf32": U.rel_err(L_tc.cpu().numpy(), ref, Pp, "L"),
+           "rotation_fp32": U.rel_err(L32.double().cpu().numpy(), ref, Pp, "L"),
+           "rotation_fp64": 0.0}
+    ntr = int(lv.m2l_offsets[-1])
+    dense_flop = 2 * (Pp * Pp) ** 2 * ntr                  # algorithmic, one dense product
+    tf32_peak = 1917.3e12 * 1.1 / 2.25                      # measured bf16 x nominal tf32/bf16
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        tf32_peak = float(json.load(open(peaks_path)).get("bf16_tflops", 1917.3)) * 1e12 * 1.1 / 2.25
+    t_tc = times["tensor_3xtf32"] * 1e-3
+    line = {
+        "metric": METRIC + " (precision: level-5 M2L at P=16)",
+        "value": ntr / t_tc, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": times["tensor_3xtf32"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "3xtf32 (fp64 target sums)", "data": "synthetic",
+        "config": {"workload": "precision: uniform octree level 5 (32^3 boxes), 1M points seed 3, "
+                               "P=16, 5,398,920 M2L grouped by the 316 integer offsets", "P": Pp,
+                   "m2l": ntr, "l2_flush": True},
+        "roofline": {"bound": "tensor", "achieved": dense_flop / t_tc / 1e12,
+                     "peak": tf32_peak / 1e12, "unit": "TFLOP/s",
+                     "frac": dense_flop / t_tc / tf32_peak, "traffic": None,
+                     "kernel": "grid_gemm_kernel (tcgen05.mma kind::tf32, 3 products)",
+                     "tensor_flop_issued_per_pass": 3 * 2 * (Pp * Pp) ** 2 * 189 * nb,
+                     "peak_note": "measured bf16 burst x nominal tf32/bf16 (1.1/2.25)"},
+        "paths_ms": times,
+        "paths_translations_per_s": {k: ntr / (v * 1e-3) for k, v in times.items()},
+        "rel_err_vs_fp64_rotation": err,
+        "gpu_launches": 3,
+    }
+    c = clk.summary()
+    if c:
+        line["clocks"] = c
+    print(json.dumps(line))
+    grid.close()
+    h64.close()
+    h32.close()
+
+
 def run_batching(args):
     """Batching workload: adaptive octree (<= 64 points per leaf) over a Plummer
     sphere, P(level) = 4 + round(20 level / L_max), dual-tree M2L with theta =
@@ -412,7 +513,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0,
                     help="seconds of oracle work for the cpu_baseline leg")
     ap.add_argument("--no-oracle", action="store_true")
-    ap.add_argument("--config", default="octree", choices=["octree", "serving", "batching"],
+    ap.add_argument("--config", default="octree", choices=["octree", "serving", "batching", "precision"],
                     help="octree: the FP64 P=10 octree pass (default); serving: the request "
                          "loop; batching: the mixed-order adaptive-octree pass")
     ap.add_argument("--points", type=int, default=1 << 21, help="batching: Plummer points")
@@ -430,6 +531,9 @@ def main():
         return
     if args.config == "batching":
         run_batching(args)
+        return
+    if args.config == "precision":
+        run_precision(args)
         return
 
     import torch

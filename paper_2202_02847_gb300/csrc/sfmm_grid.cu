@@ -17,8 +17,10 @@
 //   * every 8 offsets the accumulator is read out (tcgen05.ld) and added into
 //     an FP64 accumulator in global memory (the target's sum is FP64);
 //   * operand chunks (32 of K) are staged in shared memory in the canonical
-//     K-major layout with a two-stage pipeline: the next chunk is loaded while
-//     the tensor cores work on the current one.
+//     K-major layout by 16-byte cp.async copies with a two-stage pipeline: the
+//     next chunk is in flight while the tensor cores work on the current one;
+//   * a CTA holds 128 targets (64 on grids below 16^3), so every T_u chunk
+//     read from L2 serves 128 target columns.
 // T_u are built once per grid object with the FP64 rotation-based M2L on the
 // 256 basis vectors of every offset.  Every mbarrier wait is bounded: on
 // time-out the kernel records SFMM_GRID_TIMEOUT in the status word, stops
@@ -41,7 +43,6 @@ namespace {
 
 constexpr int GP = 16;             // order of the grid operators
 constexpr int KD = GP * GP;        // 256 reals per box in the reduced layout
-constexpr int NT = 64;             // targets per CTA
 constexpr int KC = 32;             // K chunk staged in shared memory
 constexpr int FLUSH = 8;           // offsets accumulated in FP32 before an FP64 flush
 constexpr int NCODE = 343;         // offset codes ((dx+3)*7 + dy+3)*7 + dz+3
@@ -174,27 +175,34 @@ struct GemmArgs {
     int *status;
 };
 
-// One CTA: 64 targets of one child octant (a 4x4x4 block of the octant's
-// sub-grid), all 256 output rows, all 189 offsets of the octant.
+__device__ __forceinline__ void cp16(void *smem_dst, const void *gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_u32(smem_dst)), "l"(gsrc));
+}
+
+// One CTA: NT targets of one child octant (a 4x4x(NT/16) block of the
+// octant's sub-grid), all 256 output rows, all 189 offsets of the octant.
+// Operand chunks are copied into shared memory with 16-byte cp.async (no
+// register staging, every copy of a chunk in flight at once).
+template <int NT>
 __global__ void __launch_bounds__(128, 1) grid_gemm_kernel(GemmArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     constexpr int A_BYTES = KD * KC * 4;            // 32 KB per operand part
-    constexpr int B_BYTES = NT * KC * 4;            //  8 KB per operand part
+    constexpr int B_BYTES = NT * KC * 4;            //  8 or 16 KB per operand part
+    constexpr int TZ = NT / 16;                     // tile depth along z
     constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
     unsigned char *stage0 = sm;
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * STAGE);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int ns = a.nside, half_ns = ns / 2, tiles_per_dim = half_ns / 4;
-    const int tiles = tiles_per_dim * tiles_per_dim * tiles_per_dim;
+    const int ns = a.nside, half_ns = ns / 2, tpd = half_ns / 4, tpz = half_ns / TZ;
+    const int tiles = tpd * tpd * tpz;
     const int cls = blockIdx.x / tiles, tile = blockIdx.x % tiles;
     const int bx = (cls >> 2) & 1, by = (cls >> 1) & 1, bz = cls & 1;
-    const int tx = tile / (tiles_per_dim * tiles_per_dim), ty = (tile / tiles_per_dim) % tiles_per_dim,
-              tz = tile % tiles_per_dim;
+    const int tx = tile / (tpd * tpz), ty = (tile / tpz) % tpd, tz = tile % tpz;
     const int nh = ns + 6;
 
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" :: "r"(smem_u32(tslot)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(tslot)), "r"(2 * NT));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -222,9 +230,9 @@ __global__ void __launch_bounds__(128, 1) grid_gemm_kernel(GemmArgs a) {
 
     // the targets of this CTA: column j -> grid index
     auto target_of = [&](int j, int *x, int *y, int *z) {
-        *x = 2 * (tx * 4 + (j >> 4)) + bx;
-        *y = 2 * (ty * 4 + ((j >> 2) & 3)) + by;
-        *z = 2 * (tz * 4 + (j & 3)) + bz;
+        *x = 2 * (tx * 4 + (j / (4 * TZ))) + bx;
+        *y = 2 * (ty * 4 + ((j / TZ) & 3)) + by;
+        *z = 2 * (tz * TZ + (j % TZ)) + bz;
     };
 
     auto load_chunk = [&](int ci, unsigned char *st) {
@@ -234,28 +242,32 @@ __global__ void __launch_bounds__(128, 1) grid_gemm_kernel(GemmArgs a) {
         const float *th = a.thi + (long long)code * KD * KD;
         const float *tl = a.tlo + (long long)code * KD * KD;
         // A: 256 rows x 32 k, hi and lo (float4 = 4 consecutive k)
+#pragma unroll 4
         for (int i = tid; i < KD * (KC / 4); i += 128) {
             const int r = i / (KC / 4), k4 = (i % (KC / 4)) * 4;
-            const float4 vh = *reinterpret_cast<const float4 *>(th + (long long)r * KD + kc + k4);
-            const float4 vl = *reinterpret_cast<const float4 *>(tl + (long long)r * KD + kc + k4);
-            *reinterpret_cast<float4 *>(st + koff(r, k4)) = vh;
-            *reinterpret_cast<float4 *>(st + A_BYTES + koff(r, k4)) = vl;
+            cp16(st + koff(r, k4), th + (long long)r * KD + kc + k4);
+            cp16(st + A_BYTES + koff(r, k4), tl + (long long)r * KD + kc + k4);
         }
         // B: 64 targets x 32 k: source box = target - u on the halo grid
+#pragma unroll 4
         for (int i = tid; i < NT * (KC / 4); i += 128) {
             const int j = i / (KC / 4), k4 = (i % (KC / 4)) * 4;
             int x, y, z;
             target_of(j, &x, &y, &z);
             const long long sb = ((long long)(x - dx + 3) * nh + (y - dy + 3)) * nh + (z - dz + 3);
-            const float4 vh = *reinterpret_cast<const float4 *>(a.xhi + sb * KD + kc + k4);
-            const float4 vl = *reinterpret_cast<const float4 *>(a.xlo + sb * KD + kc + k4);
-            *reinterpret_cast<float4 *>(st + 2 * A_BYTES + koff(j, k4)) = vh;
-            *reinterpret_cast<float4 *>(st + 2 * A_BYTES + B_BYTES + koff(j, k4)) = vl;
+            cp16(st + 2 * A_BYTES + koff(j, k4), a.xhi + sb * KD + kc + k4);
+            cp16(st + 2 * A_BYTES + B_BYTES + koff(j, k4), a.xlo + sb * KD + kc + k4);
         }
+        asm volatile("cp.async.commit_group;");
+    };
+    // all copies of this thread landed, then visible to the tensor cores
+    auto copies_done = [&]() {
+        asm volatile("cp.async.wait_group 0;");
         asm volatile("fence.proxy.async.shared::cta;");
     };
 
     load_chunk(0, stage0);
+    copies_done();
     __syncthreads();
     uint32_t phase = 0;
     bool ok = true;
@@ -286,6 +298,7 @@ __global__ void __launch_bounds__(128, 1) grid_gemm_kernel(GemmArgs a) {
         }
         first_in_group = 0;
         if (ci + 1 < nchunks) load_chunk(ci + 1, stage0 + ((ci + 1) & 1) * STAGE);
+        copies_done();
         if (!bar_wait(smem_u32(bar), phase)) {
             ok = false;
             if (tid == 0) atomicOr(a.status, STATUS_GRID_TIMEOUT);
@@ -296,9 +309,10 @@ __global__ void __launch_bounds__(128, 1) grid_gemm_kernel(GemmArgs a) {
         const bool flush = ((ci + 1) % ((KD / KC) * FLUSH) == 0) || ci + 1 == nchunks;
         if (flush) {
             // rows 32*warp + lane of both halves, 64 target columns each
-            for (int h = 0; h < 2; ++h) {
-                uint32_t v[NT];
-                const uint32_t ta = tmem + h * NT + ((uint32_t)(warp * 32) << 16);
+            for (int hc = 0; hc < 2 * (NT / 64); ++hc) {
+                const int h = hc / (NT / 64), c0 = (hc % (NT / 64)) * 64;
+                uint32_t v[64];
+                const uint32_t ta = tmem + h * NT + c0 + ((uint32_t)(warp * 32) << 16);
                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x64.b32 "
                              "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
                              "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
@@ -313,11 +327,12 @@ __global__ void __launch_bounds__(128, 1) grid_gemm_kernel(GemmArgs a) {
                              : "r"(ta));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
                 const int row = h * 128 + warp * 32 + (tid & 31);
-                for (int j = 0; j < NT; ++j) {
+                for (int jj = 0; jj < 64; ++jj) {
+                    const int j = c0 + jj;
                     int x, y, z;
                     target_of(j, &x, &y, &z);
                     double *dst = a.y + (((long long)x * ns + y) * ns + z) * KD + row;
-                    *dst += (double)__uint_as_float(v[j]);
+                    *dst += (double)__uint_as_float(v[jj]);
                 }
             }
             first_in_group = 1;
@@ -329,10 +344,11 @@ __global__ void __launch_bounds__(128, 1) grid_gemm_kernel(GemmArgs a) {
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" :: "r"(tmem));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(2 * NT));
 }
 
-constexpr int SMEM_GEMM = 2 * (2 * KD * KC * 4 + 2 * NT * KC * 4) + 64;
+template <int NT>
+constexpr int smem_gemm() { return 2 * (2 * KD * KC * 4 + 2 * NT * KC * 4) + 64; }
 
 }  // namespace
 
@@ -440,7 +456,8 @@ sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out) {
     cudaFree(dpout);
     cudaFree(dcodes);
     if (st == SFMM_OK &&
-        cudaFuncSetAttribute(grid_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GEMM) != cudaSuccess)
+        (cudaFuncSetAttribute(grid_gemm_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_gemm<64>()) != cudaSuccess ||
+         cudaFuncSetAttribute(grid_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_gemm<128>()) != cudaSuccess))
         st = SFMM_ERR_CUDA;
     if (st != SFMM_OK) {
         sfmm_grid_destroy(g);
@@ -479,9 +496,14 @@ sfmm_status sfmm_grid_m2l(sfmm_grid g, double box_size, const void *M, void *L, 
         }
     }
     pack_kernel<<<2048, 256, 0, s>>>(reinterpret_cast<const double *>(M), ns, sp, g->xhi, g->xlo);
-    const int tiles = (ns / 8) * (ns / 8) * (ns / 8);
     GemmArgs a{g->thi, g->tlo, g->xhi, g->xlo, g->y, ns, g->h->d_status};
-    grid_gemm_kernel<<<8 * tiles, 128, SMEM_GEMM, s>>>(a);
+    if (ns >= 16) {          // 128 targets per CTA: 4 x 4 x 8 blocks of an octant
+        const int tiles = (ns / 8) * (ns / 8) * (ns / 16);
+        grid_gemm_kernel<128><<<8 * tiles, 128, smem_gemm<128>(), s>>>(a);
+    } else {                 // 64 targets per CTA: 4 x 4 x 4 blocks
+        const int tiles = (ns / 8) * (ns / 8) * (ns / 8);
+        grid_gemm_kernel<64><<<8 * tiles, 128, smem_gemm<64>(), s>>>(a);
+    }
     unpack_kernel<<<2048, 256, 0, s>>>(g->y, ns, su, reinterpret_cast<double *>(L), accumulate);
     return cudaGetLastError() == cudaSuccess ? SFMM_OK : SFMM_ERR_CUDA;
 }
