@@ -16,9 +16,10 @@
 //     accumulation in tensor memory (two 128-row halves x 64 columns);
 //   * every 8 offsets the accumulator is read out (tcgen05.ld) and added into
 //     an FP64 accumulator in global memory (the target's sum is FP64);
-//   * operand chunks (32 of K) are staged in shared memory in the canonical
-//     K-major layout by 16-byte cp.async copies with a two-stage pipeline: the
-//     next chunk is in flight while the tensor cores work on the current one;
+//   * operand chunks (16 of K) are staged in shared memory in the canonical
+//     K-major layout in a four-stage pipeline: the T_u chunk is stored
+//     pre-tiled in global memory and arrives by one TMA bulk copy, the
+//     targets' source vectors are gathered by 16-byte cp.async copies;
 //   * a CTA holds 128 targets (64 on grids below 16^3), so every T_u chunk
 //     read from L2 serves 128 target columns.
 // T_u are built once per grid object with the FP64 rotation-based M2L on the
@@ -43,7 +44,10 @@ namespace {
 
 constexpr int GP = 16;             // order of the grid operators
 constexpr int KD = GP * GP;        // 256 reals per box in the reduced layout
-constexpr int KC = 32;             // K chunk staged in shared memory
+constexpr int KC = 16;             // K chunk staged in shared memory
+constexpr int NST = 4;             // pipeline stages
+constexpr int NKC = KD / KC;       // chunks per offset
+constexpr int A_PART = KD * KC * 4;   // one operand part (hi or lo) of an A chunk: 16 KB
 constexpr int FLUSH = 8;           // offsets accumulated in FP32 before an FP64 flush
 constexpr int NCODE = 343;         // offset codes ((dx+3)*7 + dy+3)*7 + dz+3
 constexpr int STATUS_GRID_TIMEOUT = 4;
@@ -148,7 +152,7 @@ __global__ void unpack_kernel(const double *y, int nside, Scales sc, double *L, 
 // operators: T[code][e'][j] from the FP64 M2L of basis vector j (raw solid of
 // order GP), converted to y = L / c in the reduced layout and split hi/lo.
 __global__ void operator_kernel(const double *L, const int *codes, int ncodes, const double *c,
-                                float *thi, float *tlo) {
+                                float *thi) {
     const long long total = (long long)ncodes * KD * KD;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -161,14 +165,17 @@ __global__ void operator_kernel(const double *L, const int *codes, int ncodes, c
         const double *s = L + ((long long)k * KD + j) * (GP * (GP + 1));
         const float v = (float)(s[n * (n + 1) + (im ? n + 1 + m : m)] / c[n * (n + 1) / 2 + m]);
         const float hi = tf32_round(v);
-        const long long o = (long long)codes[k] * KD * KD + (long long)ep * KD + j;
-        thi[o] = hi;
-        tlo[o] = v - hi;
+        // pre-tiled: [code][chunk][hi|lo][K-major core-matrix tile of 256 rows x KC]
+        const int ch = j / KC, kk = j % KC;
+        unsigned char *base = reinterpret_cast<unsigned char *>(thi) +
+                              ((long long)codes[k] * NKC + ch) * 2 * A_PART;
+        *reinterpret_cast<float *>(base + koff(ep, kk)) = hi;
+        *reinterpret_cast<float *>(base + A_PART + koff(ep, kk)) = v - hi;
     }
 }
 
 struct GemmArgs {
-    const float *thi, *tlo;     // [NCODE][KD][KD]
+    const float *thi;           // pre-tiled operators, [NCODE][NKC][hi|lo][A_PART bytes]
     const float *xhi, *xlo;     // [(ns+6)^3][KD]
     double *y;                  // [ns^3][KD]
     int nside;
@@ -179,20 +186,34 @@ __device__ __forceinline__ void cp16(void *smem_dst, const void *gsrc) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_u32(smem_dst)), "l"(gsrc));
 }
 
+// dynamic shared memory: NST stages of A (hi, lo) and B (hi, lo), then 1 KB
+// for the mbarriers, the TMEM slot, the abort flag and the 189 offset codes
+template <int NT>
+constexpr int smem_gemm() { return NST * (2 * A_PART + 2 * NT * KC * 4) + 1024; }
+
 // One CTA: NT targets of one child octant (a 4x4x(NT/16) block of the
-// octant's sub-grid), all 256 output rows, all 189 offsets of the octant.
-// Operand chunks are copied into shared memory with 16-byte cp.async (no
-// register staging, every copy of a chunk in flight at once).
+// octant's sub-grid), all 256 output rows, all 189 offsets of the octant, as
+// a pipeline of NST stages of K = 16:
+//   A (the pre-tiled T_u chunk, hi and lo, 32 KB) arrives by one TMA bulk copy
+//   completing on the stage's `full` mbarrier;
+//   B (the targets' source vectors, hi and lo) is gathered with 16-byte
+//   cp.async copies;
+//   thread 0 issues the tcgen05.mma of a stage and commits them to the stage's
+//   `mmad` mbarrier, which gates the reuse of the stage and the FP64 flushes.
 template <int NT>
 __global__ void __launch_bounds__(128, 1) grid_gemm_kernel(GemmArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    constexpr int A_BYTES = KD * KC * 4;            // 32 KB per operand part
-    constexpr int B_BYTES = NT * KC * 4;            //  8 or 16 KB per operand part
+    constexpr int B_PART = NT * KC * 4;             // 8 or 4 KB
+    constexpr int STAGE = 2 * A_PART + 2 * B_PART;
     constexpr int TZ = NT / 16;                     // tile depth along z
-    constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
-    unsigned char *stage0 = sm;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * STAGE);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    constexpr int NU = 189;                         // offsets of an octant
+    constexpr int NCH = NU * NKC;                   // chunks of a CTA
+    // after the stages: 2 x NST mbarriers, the TMEM slot, the abort flag, the offset codes
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + NST * STAGE);
+    uint64_t *mmad = full + NST;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mmad + NST);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    int *codes = reinterpret_cast<int *>(tslot + 4);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int ns = a.nside, half_ns = ns / 2, tpd = half_ns / 4, tpz = half_ns / TZ;
     const int tiles = tpd * tpd * tpz;
@@ -206,8 +227,21 @@ __global__ void __launch_bounds__(128, 1) grid_gemm_kernel(GemmArgs a) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bar)));
+        for (int i = 0; i < NST; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(full + i)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mmad + i)));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
+        *abort_flag = 0;
+        // the octant's offsets u = target - source: u_i in [-3 + b_i, 2 + b_i], max|u_i| >= 2
+        int nu = 0;
+        for (int dx = -3 + bx; dx <= 2 + bx; ++dx)
+            for (int dy = -3 + by; dy <= 2 + by; ++dy)
+                for (int dz = -3 + bz; dz <= 2 + bz; ++dz) {
+                    const int ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy, az = dz < 0 ? -dz : dz;
+                    if ((ax > ay ? (ax > az ? ax : az) : (ay > az ? ay : az)) >= 2)
+                        codes[nu++] = ((dx + 3) * 7 + (dy + 3)) * 7 + (dz + 3);
+                }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -216,99 +250,107 @@ __global__ void __launch_bounds__(128, 1) grid_gemm_kernel(GemmArgs a) {
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) |
                            ((uint32_t)(128 >> 4) << 24);
 
-    // the octant's offsets u = target - source: u_i in [-3 + b_i, 2 + b_i], max|u_i| >= 2
-    int codes[189];
-    int nu = 0;
-    for (int dx = -3 + bx; dx <= 2 + bx; ++dx)
-        for (int dy = -3 + by; dy <= 2 + by; ++dy)
-            for (int dz = -3 + bz; dz <= 2 + bz; ++dz) {
-                const int ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy, az = dz < 0 ? -dz : dz;
-                if ((ax > ay ? (ax > az ? ax : az) : (ay > az ? ay : az)) >= 2)
-                    codes[nu++] = ((dx + 3) * 7 + (dy + 3)) * 7 + (dz + 3);
-            }
-    const int nchunks = nu * (KD / KC);
-
-    // the targets of this CTA: column j -> grid index
     auto target_of = [&](int j, int *x, int *y, int *z) {
         *x = 2 * (tx * 4 + (j / (4 * TZ))) + bx;
         *y = 2 * (ty * 4 + ((j / TZ) & 3)) + by;
         *z = 2 * (tz * TZ + (j % TZ)) + bz;
     };
-
-    auto load_chunk = [&](int ci, unsigned char *st) {
-        const int ui = ci / (KD / KC), kc = (ci % (KD / KC)) * KC;
-        const int code = codes[ui];
+    // A of chunk ci: one bulk copy of the pre-tiled hi|lo chunk (thread 0 only)
+    auto load_a = [&](int ci) {
+        const int stg = ci % NST;
+        const unsigned char *src = reinterpret_cast<const unsigned char *>(a.thi) +
+                                   ((long long)codes[ci / NKC] * NKC + ci % NKC) * 2 * A_PART;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                     :: "r"(smem_u32(full + stg)), "r"(2 * A_PART) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     :: "r"(smem_u32(sm + stg * STAGE)), "l"(src), "r"(2 * A_PART), "r"(smem_u32(full + stg))
+                     : "memory");
+    };
+    // B of chunk ci: the targets' source vectors, 16-byte copies by every thread
+    auto load_b = [&](int ci) {
+        unsigned char *st = sm + (ci % NST) * STAGE + 2 * A_PART;
+        const int code = codes[ci / NKC], kc = (ci % NKC) * KC;
         const int dx = code / 49 - 3, dy = (code / 7) % 7 - 3, dz = code % 7 - 3;
-        const float *th = a.thi + (long long)code * KD * KD;
-        const float *tl = a.tlo + (long long)code * KD * KD;
-        // A: 256 rows x 32 k, hi and lo (float4 = 4 consecutive k)
-#pragma unroll 4
-        for (int i = tid; i < KD * (KC / 4); i += 128) {
-            const int r = i / (KC / 4), k4 = (i % (KC / 4)) * 4;
-            cp16(st + koff(r, k4), th + (long long)r * KD + kc + k4);
-            cp16(st + A_BYTES + koff(r, k4), tl + (long long)r * KD + kc + k4);
-        }
-        // B: 64 targets x 32 k: source box = target - u on the halo grid
-#pragma unroll 4
+#pragma unroll
         for (int i = tid; i < NT * (KC / 4); i += 128) {
             const int j = i / (KC / 4), k4 = (i % (KC / 4)) * 4;
             int x, y, z;
             target_of(j, &x, &y, &z);
             const long long sb = ((long long)(x - dx + 3) * nh + (y - dy + 3)) * nh + (z - dz + 3);
-            cp16(st + 2 * A_BYTES + koff(j, k4), a.xhi + sb * KD + kc + k4);
-            cp16(st + 2 * A_BYTES + B_BYTES + koff(j, k4), a.xlo + sb * KD + kc + k4);
+            cp16(st + koff(j, k4), a.xhi + sb * KD + kc + k4);
+            cp16(st + B_PART + koff(j, k4), a.xlo + sb * KD + kc + k4);
         }
-        asm volatile("cp.async.commit_group;");
     };
-    // all copies of this thread landed, then visible to the tensor cores
-    auto copies_done = [&]() {
-        asm volatile("cp.async.wait_group 0;");
-        asm volatile("fence.proxy.async.shared::cta;");
+    // A failed wait sets the abort flag; every thread reads it only after a
+    // __syncthreads that follows the write, so all threads leave the loop at
+    // the same iteration.
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicOr(a.status, STATUS_GRID_TIMEOUT);
     };
 
-    load_chunk(0, stage0);
-    copies_done();
-    __syncthreads();
-    uint32_t phase = 0;
-    bool ok = true;
-    int first_in_group = 1;
-    for (int ci = 0; ci < nchunks; ++ci) {
-        unsigned char *st = stage0 + (ci & 1) * STAGE;
+    int a_issued = 0, a_consumed = 0, last_mma = -1, first_in_group = 1;   // thread 0's bookkeeping
+    for (int c = 0; c < NST - 1; ++c) {
+        if (tid == 0) { load_a(c); a_issued = c + 1; }
+        load_b(c);
+        asm volatile("cp.async.commit_group;");
+    }
+    for (int ci = 0; ci < NCH; ++ci) {
+        const int stg = ci % NST;
+        const uint32_t par = (uint32_t)((ci / NST) & 1);
+        // this thread's B copies of chunk ci are done (later chunks stay in flight)
+        asm volatile("cp.async.wait_group %0;" :: "n"(NST - 2));
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
+        if (*abort_flag) break;
         if (tid == 0) {
-            const uint32_t sa = smem_u32(st);
-            for (int h = 0; h < 2; ++h)
-                for (int s = 0; s < KC / 8; ++s) {
-                    const uint64_t ahi = sdesc(sa + h * (A_BYTES / 2) + s * 256, 128, 1024);
-                    const uint64_t alo = sdesc(sa + A_BYTES + h * (A_BYTES / 2) + s * 256, 128, 1024);
-                    const uint64_t bhi = sdesc(sa + 2 * A_BYTES + s * 256, 128, 1024);
-                    const uint64_t blo = sdesc(sa + 2 * A_BYTES + B_BYTES + s * 256, 128, 1024);
-                    const uint32_t d = tmem + h * NT;
-                    const uint32_t acc0 = (first_in_group && s == 0) ? 0u : 1u;
-                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-                                 :: "r"(d), "l"(ahi), "l"(bhi), "r"(idesc), "r"(acc0));
-                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
-                                 :: "r"(d), "l"(ahi), "l"(blo), "r"(idesc));
-                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
-                                 :: "r"(d), "l"(alo), "l"(bhi), "r"(idesc));
-                }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(smem_u32(bar)));
+            if (!bar_wait(smem_u32(full + stg), par)) {
+                fail();
+            } else {
+                a_consumed = ci + 1;
+                const uint32_t sa = smem_u32(sm + stg * STAGE);
+                for (int h = 0; h < 2; ++h)
+                    for (int s = 0; s < KC / 8; ++s) {
+                        const uint64_t ahi = sdesc(sa + h * (A_PART / 2) + s * 256, 128, (KC / 4) * 128);
+                        const uint64_t alo = sdesc(sa + A_PART + h * (A_PART / 2) + s * 256, 128, (KC / 4) * 128);
+                        const uint64_t bhi = sdesc(sa + 2 * A_PART + s * 256, 128, (KC / 4) * 128);
+                        const uint64_t blo = sdesc(sa + 2 * A_PART + B_PART + s * 256, 128, (KC / 4) * 128);
+                        const uint32_t d = tmem + h * NT;
+                        const uint32_t acc0 = (first_in_group && s == 0) ? 0u : 1u;
+                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                                     :: "r"(d), "l"(ahi), "l"(bhi), "r"(idesc), "r"(acc0));
+                        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
+                                     :: "r"(d), "l"(ahi), "l"(blo), "r"(idesc));
+                        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
+                                     :: "r"(d), "l"(alo), "l"(bhi), "r"(idesc));
+                    }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(smem_u32(mmad + stg)));
+                last_mma = ci;
+                first_in_group = 0;
+            }
         }
-        first_in_group = 0;
-        if (ci + 1 < nchunks) load_chunk(ci + 1, stage0 + ((ci + 1) & 1) * STAGE);
-        copies_done();
-        if (!bar_wait(smem_u32(bar), phase)) {
-            ok = false;
-            if (tid == 0) atomicOr(a.status, STATUS_GRID_TIMEOUT);
-            break;
+        // refill the stage of chunk ci - 1 with chunk ci + NST - 1 once the MMAs of ci - 1 are done
+        const int nc = ci + NST - 1;
+        if (nc < NCH) {
+            if (ci == 0 || bar_wait(smem_u32(mmad + (ci - 1) % NST), (uint32_t)(((ci - 1) / NST) & 1))) {
+                if (tid == 0) { load_a(nc); a_issued = nc + 1; }
+                load_b(nc);
+            } else {
+                fail();
+            }
         }
-        phase ^= 1;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const bool flush = ((ci + 1) % ((KD / KC) * FLUSH) == 0) || ci + 1 == nchunks;
-        if (flush) {
-            // rows 32*warp + lane of both halves, 64 target columns each
+        asm volatile("cp.async.commit_group;");
+        if ((ci + 1) % (NKC * FLUSH) == 0 || ci + 1 == NCH) {
+            // FP32 partial sums of the last FLUSH offsets -> FP64 accumulators
+            if (tid == 0 && !*abort_flag && !bar_wait(smem_u32(mmad + stg), par)) fail();
+            __syncthreads();
+            if (*abort_flag) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            // rows 32 * warp + lane of both halves, NT target columns each
             for (int hc = 0; hc < 2 * (NT / 64); ++hc) {
                 const int h = hc / (NT / 64), c0 = (hc % (NT / 64)) * 64;
                 uint32_t v[64];
@@ -327,35 +369,36 @@ __global__ void __launch_bounds__(128, 1) grid_gemm_kernel(GemmArgs a) {
                              : "r"(ta));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
                 const int row = h * 128 + warp * 32 + (tid & 31);
+#pragma unroll
                 for (int jj = 0; jj < 64; ++jj) {
-                    const int j = c0 + jj;
                     int x, y, z;
-                    target_of(j, &x, &y, &z);
+                    target_of(c0 + jj, &x, &y, &z);
                     double *dst = a.y + (((long long)x * ns + y) * ns + z) * KD + row;
                     *dst += (double)__uint_as_float(v[jj]);
                 }
             }
             first_in_group = 1;
-            asm volatile("tcgen05.fence::before_thread_sync;");
         }
-        __syncthreads();
     }
-    (void)ok;
+    // drain: no copy or MMA of this CTA may outlive it
+    asm volatile("cp.async.wait_group 0;");
+    if (tid == 0) {
+        if (last_mma >= 0 && !bar_wait(smem_u32(mmad + last_mma % NST), (uint32_t)((last_mma / NST) & 1))) fail();
+        for (int c = a_consumed; c < a_issued; ++c)
+            if (!bar_wait(smem_u32(full + c % NST), (uint32_t)((c / NST) & 1))) fail();
+    }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(2 * NT));
 }
 
-template <int NT>
-constexpr int smem_gemm() { return 2 * (2 * KD * KC * 4 + 2 * NT * KC * 4) + 64; }
-
 }  // namespace
 
 struct sfmm_grid_ctx {
     sfmm_handle h = nullptr;
     int P = GP, nside = 0;
-    float *thi = nullptr, *tlo = nullptr;    // operators
+    float *thi = nullptr;                    // operators, pre-tiled hi|lo chunks
     float *xhi = nullptr, *xlo = nullptr;    // packed sources on the halo grid
     double *y = nullptr;                     // FP64 accumulators
     double *c = nullptr;                     // sqrt((n-m)!(n+m)!) on the device
@@ -375,15 +418,14 @@ sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out) {
     g->h = h;
     g->nside = nside;
     const long long nh = nside + 6;
-    bool ok = cudaMalloc(&g->thi, sizeof(float) * (size_t)NCODE * KD * KD) == cudaSuccess &&
-              cudaMalloc(&g->tlo, sizeof(float) * (size_t)NCODE * KD * KD) == cudaSuccess &&
+    const size_t op_bytes = (size_t)NCODE * NKC * 2 * A_PART;
+    bool ok = cudaMalloc(&g->thi, op_bytes) == cudaSuccess &&
               cudaMalloc(&g->xhi, sizeof(float) * (size_t)(nh * nh * nh) * KD) == cudaSuccess &&
               cudaMalloc(&g->xlo, sizeof(float) * (size_t)(nh * nh * nh) * KD) == cudaSuccess &&
               cudaMalloc(&g->y, sizeof(double) * (size_t)nside * nside * nside * KD) == cudaSuccess &&
               cudaMalloc(&g->c, sizeof(double) * GP * (GP + 1) / 2) == cudaSuccess;
     if (!ok) { sfmm_grid_destroy(g); return SFMM_ERR_NOMEM; }
-    cudaMemset(g->thi, 0, sizeof(float) * (size_t)NCODE * KD * KD);
-    cudaMemset(g->tlo, 0, sizeof(float) * (size_t)NCODE * KD * KD);
+    cudaMemset(g->thi, 0, op_bytes);
     std::vector<double> c(GP * (GP + 1) / 2);
     {
         std::vector<double> f(2 * GP + 1, 1.0);
@@ -446,7 +488,7 @@ sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out) {
                             reinterpret_cast<void *const *>(dpout), dshift, GP, GP, count, 0, nullptr);
     }
     if (st == SFMM_OK) {
-        operator_kernel<<<1024, 256>>>(dL, dcodes, ncodes, g->c, g->thi, g->tlo);
+        operator_kernel<<<1024, 256>>>(dL, dcodes, ncodes, g->c, g->thi);
         if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) st = SFMM_ERR_CUDA;
     }
     cudaFree(dbasis);
@@ -471,7 +513,6 @@ sfmm_status sfmm_grid_destroy(sfmm_grid g) {
     if (g == nullptr) return SFMM_OK;
     cudaDeviceSynchronize();
     cudaFree(g->thi);
-    cudaFree(g->tlo);
     cudaFree(g->xhi);
     cudaFree(g->xlo);
     cudaFree(g->y);
@@ -496,8 +537,8 @@ sfmm_status sfmm_grid_m2l(sfmm_grid g, double box_size, const void *M, void *L, 
         }
     }
     pack_kernel<<<2048, 256, 0, s>>>(reinterpret_cast<const double *>(M), ns, sp, g->xhi, g->xlo);
-    GemmArgs a{g->thi, g->tlo, g->xhi, g->xlo, g->y, ns, g->h->d_status};
-    if (ns >= 16) {          // 128 targets per CTA: 4 x 4 x 8 blocks of an octant
+    GemmArgs a{g->thi, g->xhi, g->xlo, g->y, ns, g->h->d_status};
+    if (ns % 16 == 0) {      // 128 targets per CTA: 4 x 4 x 8 blocks of an octant
         const int tiles = (ns / 8) * (ns / 8) * (ns / 16);
         grid_gemm_kernel<128><<<8 * tiles, 128, smem_gemm<128>(), s>>>(a);
     } else {                 // 64 targets per CTA: 4 x 4 x 4 blocks
