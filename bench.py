@@ -339,6 +339,7 @@ def run_precision(args):
                      "frac": dense_flop / t_tc / tf32_peak, "traffic": None,
                      "kernel": "grid_gemm_kernel (tcgen05.mma kind::tf32, 3 products)",
                      "tensor_flop_issued_per_pass": 3 * 2 * (Pp * Pp) ** 2 * 189 * nb,
+                     "issued_tflops": 3 * 2 * (Pp * Pp) ** 2 * 189 * nb / t_tc / 1e12,
                      "peak_note": "measured bf16 burst x nominal tf32/bf16 (1.1/2.25)"},
         "paths_ms": times,
         "paths_translations_per_s": {k: ntr / (v * 1e-3) for k, v in times.items()},

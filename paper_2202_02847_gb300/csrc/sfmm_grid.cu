@@ -26,6 +26,7 @@
 // 256 basis vectors of every offset.  Every mbarrier wait is bounded: on
 // time-out the kernel records SFMM_GRID_TIMEOUT in the status word, stops
 // issuing work, frees its tensor memory and returns.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -49,6 +50,8 @@ constexpr int NST = 4;             // pipeline stages
 constexpr int NKC = KD / KC;       // chunks per offset
 constexpr int A_PART = KD * KC * 4;   // one operand part (hi or lo) of an A chunk: 16 KB
 constexpr int FLUSH = 8;           // offsets accumulated in FP32 before an FP64 flush
+constexpr int NU = 189;            // offsets of a child octant
+constexpr int NCH_ALL = NU * NKC;  // K chunks of a tile
 constexpr int NCODE = 343;         // offset codes ((dx+3)*7 + dy+3)*7 + dz+3
 constexpr int STATUS_GRID_TIMEOUT = 4;
 
@@ -66,14 +69,17 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// shared-memory matrix descriptor: K-major, no swizzle, core matrices of
-// 8 rows x 16 bytes; lbo = byte step between core matrices along K, sbo = along M/N
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// shared-memory matrix descriptor of a K-major operand.  layout 0: no swizzle,
+// core matrices of 8 rows x 16 bytes, lbo = byte step between core matrices
+// along K, sbo = along M/N.  layout 4: 64-byte swizzle, rows of 64 bytes,
+// sbo = step between groups of 8 rows (lbo unused).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFF);
     d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
     d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
     d |= (uint64_t)1 << 46;
+    d |= (uint64_t)(layout & 7) << 61;
     return d;
 }
 
@@ -88,14 +94,6 @@ __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float(r);
 }
 
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t phase) {
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 22) && !done; ++it)
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar), "r"(phase));
-    return done != 0;
-}
-
 // ----------------------------------------------------------------- kernels
 
 // per-coefficient scale factors (n(n+1)/2 + m): c/h^{n+1} for packing, c/h^n for unpacking
@@ -104,14 +102,20 @@ struct Scales {
 };
 
 // x = M c / h^{k+1} in the reduced layout on the halo grid, split into TF32 hi, lo.
+// The halo grid (side nh = nside + 6, even) is stored split by coordinate
+// parity, [px py pz][hx/2][hy/2][hz/2][KD], so that the sources of a tile of
+// same-parity targets under one offset form one dense box.
 __global__ void pack_kernel(const double *M, int nside, Scales sc, float *xhi, float *xlo) {
-    const int nh = nside + 6;
+    const int nh = nside + 6, nh2 = nh / 2;
     const long long total = (long long)nh * nh * nh * KD;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         const long long b = i / KD;
         const int e = (int)(i % KD);
-        const int hx = (int)(b / (nh * nh)) - 3, hy = (int)((b / nh) % nh) - 3, hz = (int)(b % nh) - 3;
+        const int hz2 = (int)(b % nh2), hy2 = (int)((b / nh2) % nh2), hx2 = (int)((b / nh2 / nh2) % nh2);
+        const int par = (int)(b / ((long long)nh2 * nh2 * nh2));
+        const int hx = 2 * hx2 + ((par >> 2) & 1) - 3, hy = 2 * hy2 + ((par >> 1) & 1) - 3,
+                  hz = 2 * hz2 + (par & 1) - 3;
         float v = 0.f;
         if (hx >= 0 && hx < nside && hy >= 0 && hy < nside && hz >= 0 && hz < nside) {
             int n, m;
@@ -176,185 +180,257 @@ __global__ void operator_kernel(const double *L, const int *codes, int ncodes, c
 
 struct GemmArgs {
     const float *thi;           // pre-tiled operators, [NCODE][NKC][hi|lo][A_PART bytes]
-    const float *xhi, *xlo;     // [(ns+6)^3][KD]
-    double *y;                  // [ns^3][KD]
+    double *y;                  // [ns^3][KD], FP64 sums, zeroed before the launch
     int nside;
     int *status;
 };
 
-__device__ __forceinline__ void cp16(void *smem_dst, const void *gsrc) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_u32(smem_dst)), "l"(gsrc));
+__device__ __forceinline__ bool try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    return done != 0;
 }
 
-// dynamic shared memory: NST stages of A (hi, lo) and B (hi, lo), then 1 KB
-// for the mbarriers, the TMEM slot, the abort flag and the 189 offset codes
-template <int NT>
-constexpr int smem_gemm() { return NST * (2 * A_PART + 2 * NT * KC * 4) + 1024; }
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
-// One CTA: NT targets of one child octant (a 4x4x(NT/16) block of the
-// octant's sub-grid), all 256 output rows, all 189 offsets of the octant, as
-// a pipeline of NST stages of K = 16:
-//   A (the pre-tiled T_u chunk, hi and lo, 32 KB) arrives by one TMA bulk copy
-//   completing on the stage's `full` mbarrier;
-//   B (the targets' source vectors, hi and lo) is gathered with 16-byte
-//   cp.async copies;
-//   thread 0 issues the tcgen05.mma of a stage and commits them to the stage's
-//   `mmad` mbarrier, which gates the reuse of the stage and the FP64 flushes.
+// bounded wait (2^22 polls and 2 s at most) that also gives up once another
+// role has raised the abort flag
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    if (try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (int it = 1; it < (1 << 22); ++it) {
+        if (try_wait(bar, parity)) return true;
+        if ((it & 255) == 0 && (*abort_flag || global_ns() - t0 > 2000000000ull)) return false;
+    }
+    return false;
+}
+
+// Work units: (K slab, tile) pairs in slab-major order, a slab being the K
+// chunks of GW consecutive chunks (FLUSH offsets) of a tile; one unit is one
+// FP32 accumulation group.  CTA c takes units c, c + G, c + 2G, ... so that at
+// any time all CTAs work on the same one or two slabs: the operator chunks and
+// source slices in use at once stay few and are served from L2.
+constexpr int GW = NKC * FLUSH;
+constexpr int NSLAB = (NCH_ALL + GW - 1) / GW;
+
+// dynamic shared memory: NST stages of A (hi, lo) and B (hi, lo), then 8 KB for
+// the mbarriers, the TMEM slot, the abort flag and the offset codes of the 8 octants
 template <int NT>
-__global__ void __launch_bounds__(128, 1) grid_gemm_kernel(GemmArgs a) {
+constexpr int smem_gemm() { return NST * (2 * A_PART + 2 * NT * KC * 4) + 8192; }
+
+// Persistent, warp-specialised GEMM over (K slab, tile) units dealt round-robin.
+//   warp 4, one thread: copies.  For chunk i it waits until the MMAs of chunk
+//     i - NST have freed the stage (`empty`), sets the stage's `full` mbarrier
+//     to expect the chunk's bytes and issues one bulk copy of the pre-tiled
+//     T_u chunk (A, hi and lo) and two 5-D tensor copies of the targets'
+//     source vectors (B, hi and lo, 64-byte swizzled rows).
+//   warp 5, one thread: MMA issue.  For chunk i it waits on `full`, issues the
+//     chunk's tcgen05.mma into one of two accumulator buffers and commits them
+//     to the stage's `empty` mbarrier; the last chunk of a unit is also
+//     committed to `acc_full` of its buffer.
+//   warps 0-3: epilogue.  For every unit they wait on `acc_full`, read their 32
+//     TMEM lanes (rows) of the buffer, add the FP32 partial sums into the FP64
+//     target sums with atomic adds (the slabs of a tile are spread over CTAs),
+//     and arrive on `acc_empty`, which the MMA thread waits on before it reuses
+//     the buffer.  The epilogue of one unit overlaps the MMAs of the next.
+// Every wait is bounded; a time-out sets the abort flag and the status word,
+// the other roles give up their waits, the copy and MMA threads wait (bounded)
+// for their work in flight, and the CTA frees its tensor memory and returns.
+template <int NT>
+__global__ void __launch_bounds__(192, 1)
+grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo) {
     extern __shared__ __align__(1024) unsigned char sm[];
     constexpr int B_PART = NT * KC * 4;             // 8 or 4 KB
     constexpr int STAGE = 2 * A_PART + 2 * B_PART;
     constexpr int TZ = NT / 16;                     // tile depth along z
-    constexpr int NU = 189;                         // offsets of an octant
-    constexpr int NCH = NU * NKC;                   // chunks of a CTA
-    // after the stages: 2 x NST mbarriers, the TMEM slot, the abort flag, the offset codes
+    constexpr uint32_t TCOLS = 4 * NT;              // 2 buffers x 2 row halves x NT columns
     uint64_t *full = reinterpret_cast<uint64_t *>(sm + NST * STAGE);
-    uint64_t *mmad = full + NST;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mmad + NST);
+    uint64_t *empty = full + NST;
+    uint64_t *acc_full = empty + NST;
+    uint64_t *acc_empty = acc_full + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(acc_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
-    int *codes = reinterpret_cast<int *>(tslot + 4);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    int *codes = reinterpret_cast<int *>(sm + NST * STAGE + 1024);   // [8][NU]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ns = a.nside, half_ns = ns / 2, tpd = half_ns / 4, tpz = half_ns / TZ;
     const int tiles = tpd * tpd * tpz;
-    const int cls = blockIdx.x / tiles, tile = blockIdx.x % tiles;
-    const int bx = (cls >> 2) & 1, by = (cls >> 1) & 1, bz = cls & 1;
-    const int tx = tile / (tpd * tpz), ty = (tile / tpz) % tpd, tz = tile % tpz;
-    const int nh = ns + 6;
+    const int n_tiles = 8 * tiles;
+    const int n_units = NSLAB * n_tiles;
+    const int G = gridDim.x;
 
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(tslot)), "r"(2 * NT));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(tslot)), "r"(TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (tid == 0) {
+    if (tid == 32) {
         for (int i = 0; i < NST; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(full + i)));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mmad + i)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(empty + i)));
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(acc_full + b)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" :: "r"(smem_u32(acc_empty + b)));
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
         *abort_flag = 0;
-        // the octant's offsets u = target - source: u_i in [-3 + b_i, 2 + b_i], max|u_i| >= 2
+    }
+    if (tid >= 64 && tid < 72) {
+        // octant o: offsets u = target - source with u_i in [-3 + b_i, 2 + b_i], max|u_i| >= 2
+        const int o = tid - 64, bx = (o >> 2) & 1, by = (o >> 1) & 1, bz = o & 1;
         int nu = 0;
         for (int dx = -3 + bx; dx <= 2 + bx; ++dx)
             for (int dy = -3 + by; dy <= 2 + by; ++dy)
                 for (int dz = -3 + bz; dz <= 2 + bz; ++dz) {
                     const int ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy, az = dz < 0 ? -dz : dz;
                     if ((ax > ay ? (ax > az ? ax : az) : (ay > az ? ay : az)) >= 2)
-                        codes[nu++] = ((dx + 3) * 7 + (dy + 3)) * 7 + (dz + 3);
+                        codes[o * NU + nu++] = ((dx + 3) * 7 + (dy + 3)) * 7 + (dz + 3);
                 }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tslot;
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) |
-                           ((uint32_t)(128 >> 4) << 24);
-
-    auto target_of = [&](int j, int *x, int *y, int *z) {
-        *x = 2 * (tx * 4 + (j / (4 * TZ))) + bx;
-        *y = 2 * (ty * 4 + ((j / TZ) & 3)) + by;
-        *z = 2 * (tz * TZ + (j % TZ)) + bz;
-    };
-    // A of chunk ci: one bulk copy of the pre-tiled hi|lo chunk (thread 0 only)
-    auto load_a = [&](int ci) {
-        const int stg = ci % NST;
-        const unsigned char *src = reinterpret_cast<const unsigned char *>(a.thi) +
-                                   ((long long)codes[ci / NKC] * NKC + ci % NKC) * 2 * A_PART;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                     :: "r"(smem_u32(full + stg)), "r"(2 * A_PART) : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     :: "r"(smem_u32(sm + stg * STAGE)), "l"(src), "r"(2 * A_PART), "r"(smem_u32(full + stg))
-                     : "memory");
-    };
-    // B of chunk ci: the targets' source vectors, 16-byte copies by every thread
-    auto load_b = [&](int ci) {
-        unsigned char *st = sm + (ci % NST) * STAGE + 2 * A_PART;
-        const int code = codes[ci / NKC], kc = (ci % NKC) * KC;
-        const int dx = code / 49 - 3, dy = (code / 7) % 7 - 3, dz = code % 7 - 3;
-#pragma unroll
-        for (int i = tid; i < NT * (KC / 4); i += 128) {
-            const int j = i / (KC / 4), k4 = (i % (KC / 4)) * 4;
-            int x, y, z;
-            target_of(j, &x, &y, &z);
-            const long long sb = ((long long)(x - dx + 3) * nh + (y - dy + 3)) * nh + (z - dz + 3);
-            cp16(st + koff(j, k4), a.xhi + sb * KD + kc + k4);
-            cp16(st + B_PART + koff(j, k4), a.xlo + sb * KD + kc + k4);
-        }
-    };
-    // A failed wait sets the abort flag; every thread reads it only after a
-    // __syncthreads that follows the write, so all threads leave the loop at
-    // the same iteration.
     auto fail = [&]() {
         *abort_flag = 1;
         atomicOr(a.status, STATUS_GRID_TIMEOUT);
     };
 
-    int a_issued = 0, a_consumed = 0, last_mma = -1, first_in_group = 1;   // thread 0's bookkeeping
-    for (int c = 0; c < NST - 1; ++c) {
-        if (tid == 0) { load_a(c); a_issued = c + 1; }
-        load_b(c);
-        asm volatile("cp.async.commit_group;");
-    }
-    for (int ci = 0; ci < NCH; ++ci) {
-        const int stg = ci % NST;
-        const uint32_t par = (uint32_t)((ci / NST) & 1);
-        // this thread's B copies of chunk ci are done (later chunks stay in flight)
-        asm volatile("cp.async.wait_group %0;" :: "n"(NST - 2));
-        asm volatile("fence.proxy.async.shared::cta;");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (*abort_flag) break;
-        if (tid == 0) {
-            if (!bar_wait(smem_u32(full + stg), par)) {
-                fail();
-            } else {
-                a_consumed = ci + 1;
-                const uint32_t sa = smem_u32(sm + stg * STAGE);
-                for (int h = 0; h < 2; ++h)
-                    for (int s = 0; s < KC / 8; ++s) {
-                        const uint64_t ahi = sdesc(sa + h * (A_PART / 2) + s * 256, 128, (KC / 4) * 128);
-                        const uint64_t alo = sdesc(sa + A_PART + h * (A_PART / 2) + s * 256, 128, (KC / 4) * 128);
-                        const uint64_t bhi = sdesc(sa + 2 * A_PART + s * 256, 128, (KC / 4) * 128);
-                        const uint64_t blo = sdesc(sa + 2 * A_PART + B_PART + s * 256, 128, (KC / 4) * 128);
-                        const uint32_t d = tmem + h * NT;
-                        const uint32_t acc0 = (first_in_group && s == 0) ? 0u : 1u;
-                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-                                     :: "r"(d), "l"(ahi), "l"(bhi), "r"(idesc), "r"(acc0));
-                        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
-                                     :: "r"(d), "l"(ahi), "l"(blo), "r"(idesc));
-                        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
-                                     :: "r"(d), "l"(alo), "l"(bhi), "r"(idesc));
+    if (warp == 4) {
+        if (lane == 0) {
+            long long i = 0;
+            long long last[NST];
+            for (int s = 0; s < NST; ++s) last[s] = -1;
+            bool ok = true;
+            for (int u = blockIdx.x; u < n_units && ok; u += G) {
+                const int tile_g = u % n_tiles, c_begin = (u / n_tiles) * GW;
+                const int c_end = (c_begin + GW < NCH_ALL) ? c_begin + GW : NCH_ALL;
+                const int cls = tile_g / tiles, tile = tile_g % tiles;
+                const int bx = (cls >> 2) & 1, by = (cls >> 1) & 1, bz = cls & 1;
+                const int tx = tile / (tpd * tpz), ty = (tile / tpz) % tpd, tz = tile % tpz;
+                int c1 = 0, c2 = 0, c3 = 0, c4 = 0;
+                const unsigned char *abase = nullptr;
+                for (int ci = c_begin; ci < c_end; ++ci, ++i) {
+                    if (ci == c_begin || ci % NKC == 0) {
+                        const int code = codes[cls * NU + ci / NKC];
+                        const int sx = bx - (code / 49 - 3) + 3, sy = by - ((code / 7) % 7 - 3) + 3,
+                                  sz = bz - (code % 7 - 3) + 3;
+                        c1 = tz * TZ + (sz >> 1);
+                        c2 = ty * 4 + (sy >> 1);
+                        c3 = tx * 4 + (sx >> 1);
+                        c4 = ((sx & 1) << 2) | ((sy & 1) << 1) | (sz & 1);
+                        abase = reinterpret_cast<const unsigned char *>(a.thi) + (long long)code * NKC * 2 * A_PART;
                     }
+                    const int stg = (int)(i % NST), kc = (ci % NKC) * KC;
+                    if (i >= NST && !wait_or_abort(smem_u32(empty + stg), (uint32_t)(((i / NST) - 1) & 1), abort_flag)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t dst = smem_u32(sm + stg * STAGE), bar = smem_u32(full + stg);
+                    const unsigned char *src = abase + (long long)(ci % NKC) * 2 * A_PART;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(STAGE) : "memory");
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 :: "r"(dst), "l"(src), "r"(2 * A_PART), "r"(bar) : "memory");
+                    asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                                 " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+                                 :: "r"(dst + 2 * A_PART), "l"(reinterpret_cast<uint64_t>(&tm_hi)),
+                                    "r"(kc), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar) : "memory");
+                    asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                                 " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+                                 :: "r"(dst + 2 * A_PART + B_PART), "l"(reinterpret_cast<uint64_t>(&tm_lo)),
+                                    "r"(kc), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar) : "memory");
+                    last[stg] = i;
+                }
+            }
+            // drain: every copy issued has landed before the CTA frees its memory
+            for (int s = 0; s < NST; ++s)
+                if (last[s] >= 0 && !wait_or_abort(smem_u32(full + s), (uint32_t)((last[s] / NST) & 1), abort_flag)) fail();
+        }
+        __syncwarp();
+    } else if (warp == 5) {
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) |
+                                   ((uint32_t)(128 >> 4) << 24);
+            // descriptors of stage 0; stage s adds s * STAGE to the address field
+            const uint32_t s0 = smem_u32(sm);
+            const uint64_t dA = sdesc(s0, 128, (KC / 4) * 128, 0);
+            const uint64_t dB = sdesc(s0 + 2 * A_PART, 16, 512, 4);
+            long long i = 0, g = 0, last_mma = -1;
+            bool ok = true;
+            for (int u = blockIdx.x; u < n_units && ok; u += G, ++g) {
+                const int c_begin = (u / n_tiles) * GW;
+                const int c_end = (c_begin + GW < NCH_ALL) ? c_begin + GW : NCH_ALL;
+                const int b = (int)(g & 1);
+                if (g >= 2 && !wait_or_abort(smem_u32(acc_empty + b), (uint32_t)(((g >> 1) - 1) & 1), abort_flag)) {
+                    fail();
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t dcol = tmem + (uint32_t)b * 2 * NT;
+                for (int ci = c_begin; ci < c_end; ++ci, ++i) {
+                    const int stg = (int)(i % NST);
+                    if (!wait_or_abort(smem_u32(full + stg), (uint32_t)((i / NST) & 1), abort_flag)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint64_t so = (uint64_t)((stg * STAGE) >> 4);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+#pragma unroll
+                        for (int s = 0; s < KC / 8; ++s) {
+                            const uint64_t ahi = dA + so + ((h * (A_PART / 2) + s * 256) >> 4);
+                            const uint64_t alo = ahi + (A_PART >> 4);
+                            const uint64_t bhi = dB + so + ((s * 32) >> 4);
+                            const uint64_t blo = bhi + (B_PART >> 4);
+                            const uint32_t d = dcol + h * NT;
+                            const uint32_t acc0 = (ci == c_begin && s == 0) ? 0u : 1u;
+                            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                                         :: "r"(d), "l"(ahi), "l"(bhi), "r"(idesc), "r"(acc0));
+                            asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
+                                         :: "r"(d), "l"(ahi), "l"(blo), "r"(idesc));
+                            asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
+                                         :: "r"(d), "l"(alo), "l"(bhi), "r"(idesc));
+                        }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(smem_u32(empty + stg)) : "memory");
+                    last_mma = i;
+                }
+                if (!ok) break;
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             :: "r"(smem_u32(mmad + stg)));
-                last_mma = ci;
-                first_in_group = 0;
+                             :: "r"(smem_u32(acc_full + b)) : "memory");
             }
+            // drain: the MMAs issued have completed before the CTA frees its memory
+            if (last_mma >= 0 && !wait_or_abort(smem_u32(empty + last_mma % NST), (uint32_t)((last_mma / NST) & 1), abort_flag)) fail();
         }
-        // refill the stage of chunk ci - 1 with chunk ci + NST - 1 once the MMAs of ci - 1 are done
-        const int nc = ci + NST - 1;
-        if (nc < NCH) {
-            if (ci == 0 || bar_wait(smem_u32(mmad + (ci - 1) % NST), (uint32_t)(((ci - 1) / NST) & 1))) {
-                if (tid == 0) { load_a(nc); a_issued = nc + 1; }
-                load_b(nc);
-            } else {
-                fail();
+        __syncwarp();
+    } else {
+        long long g = 0;
+        for (int u = blockIdx.x; u < n_units; u += G, ++g) {
+            const int tile_g = u % n_tiles;
+            const int b = (int)(g & 1);
+            bool ok = true;
+            if (lane == 0) ok = wait_or_abort(smem_u32(acc_full + b), (uint32_t)((g >> 1) & 1), abort_flag);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) {
+                if (lane == 0) fail();
+                break;
             }
-        }
-        asm volatile("cp.async.commit_group;");
-        if ((ci + 1) % (NKC * FLUSH) == 0 || ci + 1 == NCH) {
-            // FP32 partial sums of the last FLUSH offsets -> FP64 accumulators
-            if (tid == 0 && !*abort_flag && !bar_wait(smem_u32(mmad + stg), par)) fail();
-            __syncthreads();
-            if (*abort_flag) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            // rows 32 * warp + lane of both halves, NT target columns each
+            const int cls = tile_g / tiles, tile = tile_g % tiles;
+            const int bx = (cls >> 2) & 1, by = (cls >> 1) & 1, bz = cls & 1;
+            const int tx = tile / (tpd * tpz), ty = (tile / tpz) % tpd, tz = tile % tpz;
             for (int hc = 0; hc < 2 * (NT / 64); ++hc) {
                 const int h = hc / (NT / 64), c0 = (hc % (NT / 64)) * 64;
                 uint32_t v[64];
-                const uint32_t ta = tmem + h * NT + c0 + ((uint32_t)(warp * 32) << 16);
+                const uint32_t ta = tmem + (uint32_t)b * 2 * NT + h * NT + c0 + ((uint32_t)(warp * 32) << 16);
                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x64.b32 "
                              "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
                              "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
@@ -368,29 +444,25 @@ __global__ void __launch_bounds__(128, 1) grid_gemm_kernel(GemmArgs a) {
                                "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
                              : "r"(ta));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
-                const int row = h * 128 + warp * 32 + (tid & 31);
+                const int row = h * 128 + warp * 32 + lane;
 #pragma unroll
                 for (int jj = 0; jj < 64; ++jj) {
-                    int x, y, z;
-                    target_of(c0 + jj, &x, &y, &z);
-                    double *dst = a.y + (((long long)x * ns + y) * ns + z) * KD + row;
-                    *dst += (double)__uint_as_float(v[jj]);
+                    const int j = c0 + jj;
+                    const int x = 2 * (tx * 4 + (j / (4 * TZ))) + bx;
+                    const int y = 2 * (ty * 4 + ((j / TZ) & 3)) + by;
+                    const int z = 2 * (tz * TZ + (j % TZ)) + bz;
+                    atomicAdd(a.y + (((long long)x * ns + y) * ns + z) * KD + row, (double)__uint_as_float(v[jj]));
                 }
             }
-            first_in_group = 1;
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(acc_empty + b)) : "memory");
         }
-    }
-    // drain: no copy or MMA of this CTA may outlive it
-    asm volatile("cp.async.wait_group 0;");
-    if (tid == 0) {
-        if (last_mma >= 0 && !bar_wait(smem_u32(mmad + last_mma % NST), (uint32_t)((last_mma / NST) & 1))) fail();
-        for (int c = a_consumed; c < a_issued; ++c)
-            if (!bar_wait(smem_u32(full + c % NST), (uint32_t)((c / NST) & 1))) fail();
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(2 * NT));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TCOLS));
 }
 
 }  // namespace
@@ -403,7 +475,31 @@ struct sfmm_grid_ctx {
     double *y = nullptr;                     // FP64 accumulators
     double *c = nullptr;                     // sqrt((n-m)!(n+m)!) on the device
     std::vector<double> ch;                  // and on the host
+    CUtensorMap tm_hi, tm_lo;                // 5-D maps of xhi, xlo (tile boxes of source vectors)
+    int nt = 0;                              // targets per tile: 128 or 64
 };
+
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// map of the parity-split halo grid [8][nh/2][nh/2][nh/2][KD] (innermost last)
+// with boxes of KC reals x tz x 4 x 4 boxes x 1 parity class, 64-byte swizzle
+bool encode_source_map(EncodeTiled enc, CUtensorMap *m, float *base, int nside, int tz) {
+    const cuuint64_t nh2 = (cuuint64_t)(nside + 6) / 2;
+    const cuuint64_t dims[5] = {(cuuint64_t)KD, nh2, nh2, nh2, 8};
+    const cuuint64_t row = (cuuint64_t)KD * sizeof(float);
+    const cuuint64_t strides[4] = {row, row * nh2, row * nh2 * nh2, row * nh2 * nh2 * nh2};
+    const cuuint32_t box[5] = {(cuuint32_t)KC, (cuuint32_t)tz, 4, 4, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -501,6 +597,16 @@ sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out) {
         (cudaFuncSetAttribute(grid_gemm_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_gemm<64>()) != cudaSuccess ||
          cudaFuncSetAttribute(grid_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_gemm<128>()) != cudaSuccess))
         st = SFMM_ERR_CUDA;
+    g->nt = (nside % 16 == 0) ? 128 : 64;
+    if (st == SFMM_OK) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || fn == nullptr ||
+            !encode_source_map(reinterpret_cast<EncodeTiled>(fn), &g->tm_hi, g->xhi, nside, g->nt / 16) ||
+            !encode_source_map(reinterpret_cast<EncodeTiled>(fn), &g->tm_lo, g->xlo, nside, g->nt / 16))
+            st = SFMM_ERR_CUDA;
+    }
     if (st != SFMM_OK) {
         sfmm_grid_destroy(g);
         return st;
@@ -537,14 +643,14 @@ sfmm_status sfmm_grid_m2l(sfmm_grid g, double box_size, const void *M, void *L, 
         }
     }
     pack_kernel<<<2048, 256, 0, s>>>(reinterpret_cast<const double *>(M), ns, sp, g->xhi, g->xlo);
-    GemmArgs a{g->thi, g->xhi, g->xlo, g->y, ns, g->h->d_status};
-    if (ns % 16 == 0) {      // 128 targets per CTA: 4 x 4 x 8 blocks of an octant
-        const int tiles = (ns / 8) * (ns / 8) * (ns / 16);
-        grid_gemm_kernel<128><<<8 * tiles, 128, smem_gemm<128>(), s>>>(a);
-    } else {                 // 64 targets per CTA: 4 x 4 x 4 blocks
-        const int tiles = (ns / 8) * (ns / 8) * (ns / 8);
-        grid_gemm_kernel<64><<<8 * tiles, 128, smem_gemm<64>(), s>>>(a);
-    }
+    // tiles of 4 x 4 x (nt / 16) same-octant targets; one persistent CTA per SM
+    // deals the (K slab, tile) units round-robin
+    GemmArgs a{g->thi, g->y, ns, g->h->d_status};
+    const int ctas = g->h->sm_count > 0 ? g->h->sm_count : 1;
+    if (g->nt == 128)
+        grid_gemm_kernel<128><<<ctas, 192, smem_gemm<128>(), s>>>(a, g->tm_hi, g->tm_lo);
+    else
+        grid_gemm_kernel<64><<<ctas, 192, smem_gemm<64>(), s>>>(a, g->tm_hi, g->tm_lo);
     unpack_kernel<<<2048, 256, 0, s>>>(g->y, ns, su, reinterpret_cast<double *>(L), accumulate);
     return cudaGetLastError() == cudaSuccess ? SFMM_OK : SFMM_ERR_CUDA;
 }

@@ -16,6 +16,7 @@ octree of Sec. 1.2):
 from dataclasses import dataclass, field
 
 import numpy as np
+from types import SimpleNamespace
 
 
 def rng(seed):
@@ -88,8 +89,8 @@ def box_index(ix, iy, iz, nside):
     return (ix * nside + iy) * nside + iz
 
 
-def _level_geometry(depth):
-    nside = 1 << depth
+def _level_geometry(depth, nside=None):
+    nside = (1 << depth) if nside is None else nside
     h = 1.0 / nside
     ijk = np.stack(np.meshgrid(np.arange(nside), np.arange(nside), np.arange(nside),
                                indexing="ij"), axis=-1).reshape(-1, 3)
@@ -97,14 +98,15 @@ def _level_geometry(depth):
     return nside, h, ijk, centres
 
 
-def _interaction_lists(depth):
+def _interaction_lists(depth, nside=None):
     """Standard FMM interaction list at a level: children of the parent's
     neighbours (including the parent itself) that are not adjacent to the
     target box.  Returns CSR arrays in target-major order, sources sorted by
-    box index within each target."""
-    nside, h, ijk, centres = _level_geometry(depth)
+    box index within each target.  ``nside`` overrides the side 2^depth (any
+    even side: a uniform grid of boxes whose parents form a grid of side/2)."""
+    nside, h, ijk, centres = _level_geometry(depth, nside)
     nbox = nside ** 3
-    if depth < 2:
+    if nside < 4:
         return (np.zeros(nbox + 1, np.int64), np.zeros(0, np.int64),
                 np.zeros((0, 3)), np.zeros(0, np.int64))
     par = ijk // 2
@@ -130,6 +132,18 @@ def _interaction_lists(depth):
     np.cumsum(counts, out=offsets[1:])
     shift = centres[tg] - centres[sr]
     return offsets, sr.astype(np.int64), shift, cd.astype(np.int64)
+
+
+def grid_level(nside):
+    """One uniform level of side ``nside`` (even) over the unit cube: box size,
+    centres and its M2L interaction lists (``m2l_offsets``, ``m2l_sources``,
+    ``m2l_shift``, ``m2l_code``), as for a level of ``uniform_octree``."""
+    if nside < 2 or nside % 2:
+        raise ValueError("grid side must be even")
+    _, h, ijk, centres = _level_geometry(0, nside)
+    off, src, shift, code = _interaction_lists(0, nside)
+    return SimpleNamespace(nside=nside, h=h, ijk=ijk, centres=centres, m2l_offsets=off,
+                           m2l_sources=src, m2l_shift=shift, m2l_code=code)
 
 
 def uniform_octree(depth, npoints=0, seed=2):

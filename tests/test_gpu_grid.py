@@ -25,14 +25,14 @@ def env():
     h.close()
 
 
-@pytest.mark.parametrize("depth", [3, 4])
-def test_grid_m2l_matches_rotation_path_and_oracle(env, orc, depth):
+# sides 8 (64-target tiles, 8 tiles on all SMs), 16 (128-target tiles) and
+# 24 (64-target tiles, 216 tiles: CTA ranges split tiles between CTAs)
+@pytest.mark.parametrize("ns", [8, 16, 24])
+def test_grid_m2l_matches_rotation_path_and_oracle(env, orc, ns):
     import torch
     sfmm, h = env
-    ns = 1 << depth
-    tree = W.uniform_octree(depth)
-    lv = tree.levels[depth]
-    g = W.rng(300 + depth)
+    lv = W.grid_level(ns)
+    g = W.rng(300 + ns)
     # multipoles of a level from P2M of 16 random charges per box (on the device)
     nb = ns ** 3
     pos = lv.centres[:, None, :] + g.uniform(-0.5, 0.5, size=(nb, 16, 3)) * lv.h
