@@ -48,6 +48,18 @@ def m2l_flop(p):
     return 2 * p * (p + 1) * (2 * p + 1) + 14 * p * (p + 1)
 
 
+def trans_flop(p_in, p_out):
+    """Algorithmic FLOP of one rotation-based M2L from order p_in to p_out,
+    the same count split by the side that pays it: the two swaps of every
+    input row, 4 sum_{j<=p_in} j^2, and of every output row, 4 sum_{j<=p_out} j^2;
+    the z-translation of column m couples (p_out - m) output with (p_in - m)
+    input rows, 4 (p_out - m)(p_in - m); scaling and z-rotations 7p(p+1) per
+    side.  trans_flop(p, p) == m2l_flop(p)."""
+    s2 = lambda p: p * (p + 1) * (2 * p + 1) // 6
+    z = sum((p_out - m) * (p_in - m) for m in range(min(p_in, p_out)))
+    return 4 * s2(p_in) + 4 * s2(p_out) + 4 * z + 7 * p_in * (p_in + 1) + 7 * p_out * (p_out + 1)
+
+
 def m2l_bytes(p, w=8):
     """Algorithmic bytes of one M2L: solid in and out, shift, two pointers."""
     return w * (2 * p * (p + 1)) + 3 * w + 16
@@ -425,9 +437,9 @@ def run_batching(args):
     flop = 0
     for d in ap.waves:
         offs = d["host"]["offs"]
-        for op, pi, po, tb, te in d["classes"]:
-            flop += m2l_flop(max(pi, po)) * int(offs[te] - offs[tb])
-    classes = sorted({(pi, po) for d in ap.waves for _, pi, po, _, _ in d["classes"]})
+        for op, pi, po, tb, te, *_ in d["classes"]:
+            flop += trans_flop(pi, po) * int(offs[te] - offs[tb])
+    classes = sorted({(pi, po) for d in ap.waves for _, pi, po, *_ in d["classes"]})
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     peak = nsm * FP64_FMA_PER_CLK_SM * 2 * 2070e6
     line = {

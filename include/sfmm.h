@@ -136,17 +136,24 @@ sfmm_status sfmm_l2l_batch(sfmm_handle h, const void *const *in, void *const *ou
  * Interaction lists (target-major CSR), the form an FMM pass uses: for every
  * target t < n_targets,
  *   out[t] (+)= sum_{j = offsets[t]}^{offsets[t+1]-1} T(src[j], shift[3j..3j+2])
- * summed in list order j (deterministic: the same lists give bitwise the same
- * result on every run).  With accumulate == 0 out[t] is overwritten (a target
- * with an empty list receives zeros).
+ * summed in a fixed order that depends only on the lists and the handle's
+ * policy (deterministic: the same lists give bitwise the same result on every
+ * run).  With accumulate == 0 out[t] is overwritten (a target with an empty
+ * list receives zeros).
  * src    : device array of nnz = offsets[n_targets] device pointers (order p_in)
  * shift  : device array of 3*nnz reals, r = target centre - source centre
  * offsets: device array of n_targets+1 non-decreasing long long, offsets[0] = 0
  * out    : device array of n_targets distinct device pointers (order p_out),
  *          not overlapping any source
- * One GPU thread owns one target; targets whose lists have similar lengths
- * should be adjacent (the FMM planner sorts them) so that the threads of a
- * warp finish together.
+ * Work split: G lanes share a target (G = 32 for M2L, 8 for M2M and L2L), so
+ * a list of length L costs ceil(L / G) translations on the critical path.
+ * Lane i of a group sums the sources j = offsets[t] + i, + i + G, ... in
+ * order, and the G partial sums are added in lane order (the unrolled
+ * kernels add the G lanes' results round by round instead).  The generic
+ * kernels keep a lane's partial sum in the handle's global scratch; under
+ * SFMM_POLICY_SHARED, or when the scratch has no room for the orders, one
+ * thread walks each whole list in order.  Targets whose lists have similar
+ * lengths should be adjacent (the FMM planner sorts them by length).
  * Errors: as for the batch calls.
  */
 sfmm_status sfmm_translate_lists(sfmm_handle h, sfmm_op op, const void *const *src,
@@ -160,20 +167,22 @@ sfmm_status sfmm_translate_lists(sfmm_handle h, sfmm_op op, const void *const *s
  * classes of target-major lists that share one CSR (src, shift, offsets, out
  * as in sfmm_translate_lists): class k applies op_k from order p_in_k to
  * p_out_k to the targets [target_begin_k, target_end_k).  Classes may come in
- * any order and must not overlap; each class's targets are summed in list
- * order exactly as sfmm_translate_lists does.  Work is dealt to warps in
- * chunks of 32 targets of one class.  The rotated solids live in the
- * handle's global scratch, which must hold one slot for the largest p_in of
- * the call (sfmm_reserve_scratch).  classes is a HOST array (copied into the
- * launch); 1 <= n_classes <= SFMM_MAX_CLASSES.
+ * any order and must not overlap.  Class k spreads each list over
+ * lanes_per_target_k lanes and sums in the fixed order that
+ * sfmm_translate_lists uses for that many lanes (1: one thread walks the list
+ * in order).  Work is dealt to warps in chunks of 32 / lanes_per_target
+ * targets of one class.  The rotated solids (and the lanes' partial sums)
+ * live in the handle's global scratch, which must hold one slot for the
+ * largest orders of the call (sfmm_reserve_scratch).  classes is a HOST
+ * array (copied into the launch); 1 <= n_classes <= SFMM_MAX_CLASSES.
  * Errors: SFMM_ERR_ARG, SFMM_ERR_ORDER, SFMM_ERR_UNSUPPORTED (no scratch),
  * SFMM_ERR_CUDA.
  */
-#define SFMM_MAX_CLASSES 64
+#define SFMM_MAX_CLASSES 256
 typedef struct {
     int op;                   /* sfmm_op */
     int p_in, p_out;
-    int reserved;             /* 0 */
+    int lanes_per_target;     /* 0 (32 for M2L, 8 for M2M, L2L), 1, 2, 4, 8, 16 or 32 */
     long long target_begin;   /* first target of the class */
     long long target_end;     /* one past the last */
 } sfmm_list_class;
@@ -187,8 +196,11 @@ sfmm_status sfmm_translate_lists_multi(sfmm_handle h, const sfmm_list_class *cla
  * Launch policies (the tile-size choice of Sec. 3.2, made per order on the
  * GPU): which kernel variant serves (op, p_in, p_out) on this handle and how
  * many warps a block has (0 = automatic).
- *   SFMM_POLICY_AUTO     - built-in choice (unrolled if compiled, else shared,
- *                          else global scratch)
+ *   SFMM_POLICY_AUTO     - built-in choice: unrolled if compiled; else shared
+ *                          memory while two blocks of two or more warps fit
+ *                          per SM; else the global scratch (launches that use
+ *                          the scratch of one handle run one after another,
+ *                          whatever their streams)
  *   SFMM_POLICY_UNROLLED - fixed-order kernel; only p_in = p_out in {6,8,10,12}
  *   SFMM_POLICY_SHARED   - generic kernel, working set in shared memory
  *   SFMM_POLICY_GLOBAL   - generic kernel, rotated solid in the global scratch
@@ -208,9 +220,11 @@ sfmm_status sfmm_set_policy(sfmm_handle h, sfmm_op op, int p_in, int p_out,
 
 /*
  * Allocate (or grow) the handle's global scratch so that the global-scratch
- * variants can serve inputs up to order p_in_max with four resident warps per
- * SM.  Synchronous; not to be called while work using the handle is in
- * flight.  Errors: SFMM_ERR_ARG, SFMM_ERR_ORDER, SFMM_ERR_NOMEM.
+ * variants can serve orders up to p_in_max with four resident warps per SM:
+ * 2 p_in_max (p_in_max + 1) reals per lane, a rotated solid and a partial
+ * output sum (sfmm_create reserves it for P_max).  Synchronous; not to be
+ * called while work using the handle is in flight.  Errors: SFMM_ERR_ARG,
+ * SFMM_ERR_ORDER, SFMM_ERR_NOMEM.
  */
 sfmm_status sfmm_reserve_scratch(sfmm_handle h, int p_in_max);
 

@@ -55,8 +55,12 @@ class Autotuner:
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    def tune(self, op, p_in, p_out, n=8192, reps=3):
-        """Pick and install the fastest policy; returns (policy, warps, ms per n)."""
+    def tune(self, op, p_in, p_out, n=None, reps=3):
+        """Pick and install the fastest policy; returns (policy, warps, ms per n).
+        The sample (default: two full waves of 4 warps per SM) fills the GPU, so
+        that variants are compared at the occupancy they reach in production."""
+        if n is None:
+            n = max(8192, 2 * 4 * 32 * torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
         key = _key(self.dtype, op, p_in, p_out)
         if key in self.cache:
             pol, w, ms = self.cache[key]

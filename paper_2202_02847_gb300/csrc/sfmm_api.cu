@@ -38,6 +38,9 @@ void set_kernel_attrs(size_t smem) {
     set_attrs_one<T, false>(smem);
     set_attrs_one<T, true>(smem);
     cudaFuncSetAttribute(multi_lists_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(glists_kernel<T, OP_M2M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(glists_kernel<T, OP_M2L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(glists_kernel<T, OP_L2L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(p2x_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(p2x_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
@@ -147,7 +150,18 @@ Geometry pick_geometry(const sfmm_ctx *h, int op, int p_in, int p_out, long long
     const size_t sz = sizeof(T);
     const int pol = h->policy[op][p_in][p_out];
     const int wfix = h->warps[op][p_in][p_out];
-    if (pol != SFMM_POLICY_GLOBAL && shared_only_fits<T>(h, p_in, p_out)) {
+    // AUTO keeps the working set in shared memory only while two blocks of at
+    // least two warps fit per SM (one warp per sub-partition; the FP64 pipe of a
+    // sub-partition idles without one), else it takes the global scratch
+    bool shared = pol != SFMM_POLICY_GLOBAL && shared_only_fits<T>(h, p_in, p_out);
+    if (shared && pol == SFMM_POLICY_AUTO) {
+        const size_t pw = (size_t)(x_elems(p_in) + row_elems(p_in, p_out)) * WARP * sz;
+        const size_t slot_g = (size_t)x_elems(p_in) * WARP * sz;
+        const bool global_ok = h->d_scratch != nullptr && slot_g * 4 <= h->scratch_bytes &&
+                               (size_t)row_elems(p_in, p_out) * WARP * sz <= h->smem_optin;
+        if (h->smem_optin / 2 / pw < 2 && global_ok) shared = false;
+    }
+    if (shared) {
         const size_t per_warp = (size_t)(x_elems(p_in) + row_elems(p_in, p_out)) * WARP * sz;
         // aim for two resident blocks per SM (half the opt-in budget each)
         int w = (int)(h->smem_optin / 2 / per_warp);
@@ -253,11 +267,68 @@ sfmm_status launch_batch(sfmm_handle h, int op, const void *const *in, void *con
     return cudaGetLastError() == cudaSuccess ? SFMM_OK : SFMM_ERR_CUDA;
 }
 
+// Lanes per target of the generic lists kernels when the caller does not say:
+// M2L lists are long (a box's interaction list), M2M and L2L lists hold the
+// eight children or the parent.
+int default_lanes(int op) { return op == OP_M2L ? 32 : 8; }
+
+// Geometry of a group-lists launch (G lanes per target, rotated solid and
+// output slot per lane in the global scratch); warps = 0 if it cannot run.
+template <typename T>
+Geometry group_geometry(const sfmm_ctx *h, int op, int p_in, int p_out, long long n_targets, int G) {
+    Geometry g;
+    const size_t sz = sizeof(T);
+    const size_t per_warp = (size_t)row_elems(p_in, p_out) * WARP * sz;
+    const size_t slot = (size_t)(x_elems(p_in) + p_out * (p_out + 1)) * WARP * sz;
+    if (h->d_scratch == nullptr || per_warp > h->smem_optin || slot > h->scratch_bytes) return g;
+    int w = (int)(h->smem_optin / 2 / per_warp);
+    if (w < 1) w = 1;
+    if (w > 4) w = 4;
+    const int wfix = h->warps[op][p_in][p_out];
+    if (wfix > 0 && (size_t)wfix * per_warp <= h->smem_optin) w = wfix;
+    const long long slots = (long long)(h->scratch_bytes / slot);
+    if (w > slots) w = (int)slots;
+    long long blocks = slots / w;
+    const long long chunks = (n_targets + WARP / G - 1) / (WARP / G);
+    const long long need = (chunks + w - 1) / w;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) return g;
+    g.xg = true;
+    g.warps = w;
+    g.smem = (size_t)w * per_warp;
+    g.blocks = blocks;
+    return g;
+}
+
+template <typename T, int OP>
+void glists_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
+                   const T *const *Sp, const T *S, const long long *offsets, T *const *O,
+                   int p_in, int p_out, long long nt, int acc, int G, T *scratch, int *status) {
+    auto k = glists_kernel<T, OP>;
+    k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, Sp, S, offsets, O, p_in, p_out, nt, acc, G, scratch, status);
+}
+
 template <typename T>
 sfmm_status launch_lists(sfmm_handle h, int op, const void *const *src, const void *shift,
                          const long long *offsets, void *const *out, int p_in, int p_out,
                          long long n_targets, int accumulate, cudaStream_t stream,
                          const DevTables<T> &tb) {
+    // AUTO and GLOBAL: G lanes per target with the global scratch, if it has room
+    if (h->policy[op][p_in][p_out] != SFMM_POLICY_SHARED) {
+        const int G = default_lanes(op);
+        const Geometry gg = group_geometry<T>(h, op, p_in, p_out, n_targets, G);
+        if (gg.warps >= 1 && gg.blocks <= 0x7fffffffLL) {
+            auto Sp = reinterpret_cast<const T *const *>(src);
+            auto O = reinterpret_cast<T *const *>(out);
+            auto S = reinterpret_cast<const T *>(shift);
+            T *scr = reinterpret_cast<T *>(h->d_scratch);
+            ScratchGuard guard(h, stream, true);
+            if (op == OP_M2M) glists_launch<T, OP_M2M>(h, gg, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, G, scr, h->d_status);
+            else if (op == OP_M2L) glists_launch<T, OP_M2L>(h, gg, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, G, scr, h->d_status);
+            else glists_launch<T, OP_L2L>(h, gg, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, G, scr, h->d_status);
+            return cudaGetLastError() == cudaSuccess ? SFMM_OK : SFMM_ERR_CUDA;
+        }
+    }
     const Geometry g = pick_geometry<T>(h, op, p_in, p_out, n_targets);
     if (g.warps < 1) return SFMM_ERR_UNSUPPORTED;
     if (g.blocks > 0x7fffffffLL) return SFMM_ERR_UNSUPPORTED;
@@ -362,10 +433,10 @@ sfmm_status sfmm_create(int P_max, sfmm_dtype dtype, sfmm_handle *out) {
     if (st == SFMM_OK && cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) st = SFMM_ERR_CUDA;
     if (st == SFMM_OK) {
         const size_t esz = dtype == SFMM_F64 ? sizeof(double) : sizeof(float);
-        const bool fits = (size_t)(x_elems(P_max) + row_elems(P_max, P_max)) * WARP * esz <= h->smem_optin;
-        if (!fits) {
-            // four resident warps per SM, one slot per lane
-            h->scratch_bytes = (size_t)smc * 4 * WARP * x_elems(P_max) * esz;
+        {
+            // four resident warps per SM; a lane's slot holds a rotated solid and
+            // an output solid of order P_max (the group-lists kernels use both)
+            h->scratch_bytes = (size_t)smc * 4 * WARP * 2 * x_elems(P_max) * esz;
             if (cudaMalloc(&h->d_scratch, h->scratch_bytes) != cudaSuccess) st = SFMM_ERR_NOMEM;
             else if (cudaEventCreateWithFlags(&h->scratch_free, cudaEventDisableTiming) != cudaSuccess)
                 st = SFMM_ERR_CUDA;
@@ -510,7 +581,7 @@ sfmm_status sfmm_reserve_scratch(sfmm_handle h, int p_in_max) {
     if (h == nullptr) return SFMM_ERR_ARG;
     if (p_in_max < 1 || p_in_max > h->Pmax) return SFMM_ERR_ORDER;
     const size_t sz = h->dtype == SFMM_F64 ? sizeof(double) : sizeof(float);
-    const size_t need = (size_t)h->sm_count * 4 * WARP * x_elems(p_in_max) * sz;
+    const size_t need = (size_t)h->sm_count * 4 * WARP * 2 * x_elems(p_in_max) * sz;
     std::lock_guard<std::mutex> lk(h->scratch_mu);
     if (h->d_scratch != nullptr && h->scratch_bytes >= need) return SFMM_OK;
     if (cudaDeviceSynchronize() != cudaSuccess) return SFMM_ERR_CUDA;
@@ -544,11 +615,14 @@ static sfmm_status launch_multi(sfmm_handle h, const sfmm_list_class *classes, i
         m.op = c.op;
         m.p_in = c.p_in;
         m.p_out = c.p_out;
+        m.g = c.lanes_per_target > 0 ? c.lanes_per_target : default_lanes(c.op);
         m.tb = c.target_begin;
         m.te = c.target_end;
         m.chunk_begin = chunks;
-        chunks += (c.target_end - c.target_begin + WARP - 1) / WARP;
-        xs = xs > x_elems(c.p_in) ? xs : x_elems(c.p_in);
+        const int per_chunk = WARP / m.g;
+        chunks += (c.target_end - c.target_begin + per_chunk - 1) / per_chunk;
+        const int xk = x_elems(c.p_in) + (m.g > 1 ? c.p_out * (c.p_out + 1) : 0);
+        xs = xs > xk ? xs : xk;
         rs = rs > row_elems(c.p_in, c.p_out) ? rs : row_elems(c.p_in, c.p_out);
     }
     mp.total_chunks = chunks;
@@ -591,6 +665,8 @@ sfmm_status sfmm_translate_lists_multi(sfmm_handle h, const sfmm_list_class *cla
         const sfmm_list_class &c = classes[k];
         if (c.op != SFMM_M2M && c.op != SFMM_M2L && c.op != SFMM_L2L) return SFMM_ERR_ARG;
         if (c.target_begin < 0 || c.target_end < c.target_begin) return SFMM_ERR_ARG;
+        const int g = c.lanes_per_target;
+        if (g != 0 && g != 1 && g != 2 && g != 4 && g != 8 && g != 16 && g != 32) return SFMM_ERR_ARG;
         if (c.p_in < 1 || c.p_out < 1 || c.p_in > h->Pmax || c.p_out > h->Pmax) return SFMM_ERR_ORDER;
     }
     if (src == nullptr || shift == nullptr || offsets == nullptr || out == nullptr) return SFMM_ERR_ARG;

@@ -161,20 +161,26 @@ __device__ __forceinline__ void ztrans_block(const T *__restrict__ Tz, int Pm, i
     for (int j = 0; j < G; ++j) { Are[m0 + j] = ar[j]; Aim[m0 + j] = ai[j]; }
 }
 
-// Output sink: overwrite or add one coefficient of the result.
+// Output sink: overwrite or add one coefficient of the result (a solid in
+// memory, or a lane's interleaved slot in the scratch).
 template <typename T>
 __device__ __forceinline__ void put(T *dst, T v, bool add) {
     if (add) v += *dst;
     *dst = v;
 }
+template <typename T>
+__device__ __forceinline__ void put(LaneArr<T> dst, T v, bool add) {
+    if (add) v += dst[0];
+    dst[0] = v;
+}
 
 // One translation computed by the calling thread (Sec. 3.4 steps 1-4, with
 // the z-axis translation of the op).  `buf` is this lane's shared memory of
 // lane_elems(p_in, p_out) elements.  add = accumulate into dst.
-template <typename T, int OP>
+template <typename T, int OP, typename D>
 __device__ void translate_one(const DevTables<T> &tb, int p_in, int p_out,
                               const T *__restrict__ src, const T *__restrict__ shift,
-                              T *__restrict__ dst, bool add, LaneArr<T> X, LaneArr<T> buf) {
+                              D dst, bool add, LaneArr<T> X, LaneArr<T> buf) {
     const int P = p_in > p_out ? p_in : p_out;
     // lane memory map: X = rotated solid (rows k < p_in, p_in(p_in+1) elements),
     // buf = two row buffers and the powers of e^{i alpha}, e^{i beta} (8P)
@@ -265,7 +271,7 @@ __device__ void translate_one(const DevTables<T> &tb, int p_in, int p_out,
         swap_row(tb, n, Bre, Bim, Are, Aim, n + 1);
         // rotate by -alpha, undo the scaling and the basis change, store
         const T *cf = ((OP == OP_M2M) ? tb.ic : tb.c) + n * (n + 1) / 2;
-        T *orow = dst + n * (n + 1);
+        D orow = dst + n * (n + 1);
         for (int m = 0; m <= n; ++m) {
             const T f = so * ldt(cf + m);
             const T re = Are[m] * f, im = Aim[m] * f;
@@ -354,14 +360,86 @@ __global__ void __launch_bounds__(256, 1) lists_kernel(DevTables<T> tb, const T 
     }
 }
 
+// Lists with G lanes per target (G = 2, 4, 8, 16 or 32; 32/G targets per
+// warp), so that a long list is spread over the lanes of its group and a
+// target's cost is ceil(length / G) translations.  Lane `mem` of a group
+// takes the sources j0 + mem, j0 + mem + G, ... and accumulates their
+// translations in its own output slot Y (interleaved in the scratch); then
+// member mem adds the coefficients mem, mem + G, ... of the group's slots, in
+// lane order, into the target.  The order of the additions is fixed, so the
+// result does not depend on timing.
+template <typename T, int OP>
+__device__ void group_chunk(const DevTables<T> &tb, int p_in, int p_out, int G, long long t,
+                            long long t_end, const T *const *src, const T *shift,
+                            const long long *offsets, T *const *out, int accumulate,
+                            LaneArr<T> X, LaneArr<T> Y, LaneArr<T> buf, int *status) {
+    const int lane = threadIdx.x & (WARP - 1), mem = lane % G, q0 = lane - mem;
+    long long j0 = 0, j1 = 0;
+    T *dst = nullptr;
+    if (t < t_end) {
+        j0 = offsets[t];
+        j1 = offsets[t + 1];
+        dst = out[t];
+        if (j1 < j0) {
+            if (mem == 0) atomicOr(status, STATUS_BAD_OFFSETS);
+            j1 = j0;
+        }
+        if (dst == nullptr && mem == 0) atomicOr(status, STATUS_NULL_POINTER);
+    }
+    bool any = false;
+    for (long long j = j0 + mem; j < j1; j += G) {
+        const T *s = src[j];
+        if (s == nullptr) { atomicOr(status, STATUS_NULL_POINTER); continue; }
+        translate_one<T, OP>(tb, p_in, p_out, s, shift + 3 * j, Y, any, X, buf);
+        any = true;
+    }
+    const unsigned has = __ballot_sync(0xffffffffu, any);
+    __syncwarp();
+    if (dst != nullptr) {
+        const int ey = p_out * (p_out + 1);
+        const LaneArr<T> Y0{Y.p - lane};               // lane 0's slot; lane i at Y0.p + i
+        for (int e = mem; e < ey; e += G) {
+            T acc = T(0);
+            for (int i = 0; i < G; ++i)
+                if ((has >> (q0 + i)) & 1u) acc += Y0.p[(size_t)e * WARP + q0 + i];
+            dst[e] = accumulate ? dst[e] + acc : acc;
+        }
+    }
+    __syncwarp();                                       // slots are reused by the next chunk
+}
+
+// Single-class lists, G lanes per target, rotated solid and output slot in the
+// global scratch (slot of x_elems(p_in) + p_out (p_out + 1) elements per lane).
+template <typename T, int OP>
+__global__ void __launch_bounds__(256, 1) glists_kernel(DevTables<T> tb, const T *const *src,
+                                                     const T *shift, const long long *offsets,
+                                                     T *const *out, int p_in, int p_out,
+                                                     long long n_targets, int accumulate, int G,
+                                                     T *scratch, int *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & (WARP - 1), warp = threadIdx.x / WARP;
+    const long long slot = (long long)blockIdx.x * (blockDim.x / WARP) + warp;
+    const int ex = x_elems(p_in), ey = p_out * (p_out + 1);
+    LaneArr<T> X{scratch + slot * (long long)(ex + ey) * WARP + lane};
+    LaneArr<T> Y = X + ex;
+    LaneArr<T> buf{reinterpret_cast<T *>(smem_raw) + (size_t)warp * row_elems(p_in, p_out) * WARP + lane};
+    const int ng = WARP / G;
+    const long long nw = (long long)gridDim.x * (blockDim.x / WARP);
+    for (long long c = slot; c * ng < n_targets; c += nw)
+        group_chunk<T, OP>(tb, p_in, p_out, G, c * ng + lane / G, n_targets, src, shift, offsets, out,
+                           accumulate, X, Y, buf, status);
+}
+
 // Several classes of lists in one persistent launch.  The class table travels
-// as a kernel parameter; chunk c (32 targets) belongs to the class k with
-// chunk_begin[k] <= c < chunk_begin[k+1].  The rotated solid lives in the
-// global scratch (slot of x_slot elements per lane); shared memory holds the
-// row buffers and powers for the largest order of the launch.
-constexpr int MAX_CLASSES = 64;
+// as a kernel parameter; chunk c belongs to the class k with
+// chunk_begin[k] <= c < chunk_begin[k+1] and holds 32 / g targets of it, g its
+// lanes per target (1: one lane walks a whole list; else as group_chunk).
+// The rotated solid (and for g > 1 the lane's output slot) lives in the global
+// scratch (slot of x_slot elements per lane); shared memory holds the row
+// buffers and powers for the largest order of the launch.
+constexpr int MAX_CLASSES = 256;
 struct MultiClass {
-    int op, p_in, p_out, pad;
+    int op, p_in, p_out, g;
     long long tb, te, chunk_begin;
 };
 struct MultiParams {
@@ -385,9 +463,23 @@ __global__ void __launch_bounds__(256, 1) multi_lists_kernel(DevTables<T> tb, Mu
     LaneArr<T> buf{reinterpret_cast<T *>(smem_raw) + (size_t)warp * mp.row_slot * WARP + lane};
     const long long nw = (long long)gridDim.x * (blockDim.x / WARP);
     for (long long c = slot; c < mp.total_chunks; c += nw) {
-        int k = 0;
-        while (k + 1 < mp.n && mp.c[k + 1].chunk_begin <= c) ++k;
+        int k = 0, hi = mp.n - 1;                     // last class with chunk_begin <= c
+        while (k < hi) {
+            const int mid = (k + hi + 1) >> 1;
+            if (mp.c[mid].chunk_begin <= c) k = mid; else hi = mid - 1;
+        }
         const MultiClass cl = mp.c[k];
+        if (cl.g > 1) {
+            const long long tg = cl.tb + (c - cl.chunk_begin) * (WARP / cl.g) + lane / cl.g;
+            const LaneArr<T> Y = X + x_elems(cl.p_in);
+            if (cl.op == OP_M2M)
+                group_chunk<T, OP_M2M>(tb, cl.p_in, cl.p_out, cl.g, tg, cl.te, src, shift, offsets, out, accumulate, X, Y, buf, status);
+            else if (cl.op == OP_M2L)
+                group_chunk<T, OP_M2L>(tb, cl.p_in, cl.p_out, cl.g, tg, cl.te, src, shift, offsets, out, accumulate, X, Y, buf, status);
+            else
+                group_chunk<T, OP_L2L>(tb, cl.p_in, cl.p_out, cl.g, tg, cl.te, src, shift, offsets, out, accumulate, X, Y, buf, status);
+            continue;
+        }
         const long long t = cl.tb + (c - cl.chunk_begin) * WARP + lane;
         if (t >= cl.te) continue;
         T *dst = out[t];

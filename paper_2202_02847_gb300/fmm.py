@@ -142,6 +142,15 @@ class UniformPass:
         return len(self.m2m) + 1 + len(self.l2l)
 
 
+def lanes_for_length(lengths):
+    """Lanes per target for lists of the given lengths: the smallest power of
+    two >= the length, capped at 32 (one warp); 1 for lists of 0 or 1 source.
+    A list then costs ceil(length / lanes) translations on the critical path
+    and at most half of a group's lanes idle."""
+    n = np.maximum(np.asarray(lengths, np.int64), 1)
+    return np.minimum(32, 1 << np.ceil(np.log2(n)).astype(np.int64))
+
+
 class AdaptivePass:
     """Translation pass of an adaptive octree with the expansion order rising
     with the level (mixed p_in != p_out in M2M, M2L and L2L).
@@ -212,18 +221,26 @@ class AdaptivePass:
         for w in range(int(wave.max()) + 1 if len(wave) else 0):
             sel = np.nonzero(wave == w)[0]
             ws, wt, wpi, wpo = src[sel], tgt[sel], pin[sel], pout[sel]
-            oo = np.lexsort((ws, wt, wpo, wpi))          # classes contiguous, then targets
+            # classes contiguous; inside a class, targets by decreasing list length
+            # (a warp's 32 lanes take 32 consecutive targets and run as long as the
+            # longest list), then by target and source
+            _, tinv, tcnt = np.unique(wt, return_inverse=True, return_counts=True)
+            oo = np.lexsort((ws, wt, -tcnt[tinv], wpo, wpi))
             ws, wt, wpi, wpo = ws[oo], wt[oo], wpi[oo], wpo[oo]
             newt = np.ones(len(ws), bool)
             newt[1:] = wt[1:] != wt[:-1]
             rows = np.nonzero(newt)[0]
             offs = np.concatenate([rows, [len(ws)]]).astype(np.int64)
             row_tgt, row_pi, row_po = wt[rows], wpi[rows], wpo[rows]
+            # lanes per target: the power of two >= the list length, at most 32
+            # (monotone in the length, so equal values are contiguous in a class)
+            row_lanes = lanes_for_length(np.diff(offs))
             classes = []
             cs = 0
             for r in range(1, len(rows) + 1):
-                if r == len(rows) or row_pi[r] != row_pi[cs] or row_po[r] != row_po[cs]:
-                    classes.append(("m2l", int(row_pi[cs]), int(row_po[cs]), cs, r))
+                if (r == len(rows) or row_pi[r] != row_pi[cs] or row_po[r] != row_po[cs]
+                        or row_lanes[r] != row_lanes[cs]):
+                    classes.append(("m2l", int(row_pi[cs]), int(row_po[cs]), cs, r, int(row_lanes[cs])))
                     cs = r
             self.waves.append(dict(
                 classes=classes, n=len(rows),
@@ -287,7 +304,7 @@ class AdaptivePass:
                                            d["shift"], d["offsets"], d["out"], accumulate=True,
                                            stream=stream)
         else:
-            for op, pi, po, tb, te in d["classes"]:
+            for op, pi, po, tb, te, _ in d["classes"]:
                 sfmm.translate_lists(self.h, op, d["src"], d["shift"], d["offsets"][tb:],
                                      d["out"][tb:], pi, po, te - tb, accumulate=True, stream=stream)
 
@@ -321,7 +338,7 @@ class AdaptivePass:
         for d in self.l2l:
             pairs.add(("l2l", d["p_in"], d["p_out"]))
         for d in self.waves:
-            for op, pi, po, _, _ in d["classes"]:
+            for op, pi, po, *_ in d["classes"]:
                 pairs.add((op, pi, po))
         chosen = {}
         for op, pi, po in sorted(pairs):

@@ -101,9 +101,14 @@ class TranslationServer:
                  n_streams=4, chunk=32768, inflight_per_stream=2, device="cuda", seed=5):
         self.device = torch.device(device)
         self.P_max = P_max
-        self.h = {"f64": sfmm.Handle(P_max, "f64"), "f32": sfmm.Handle(min(P_max, 29), "f32")}
         self.P32 = min(P_max, 29)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(n_streams)]
+        # one handle per stream and dtype: launches that use a handle's global
+        # scratch run one after another, so streams with their own handles overlap
+        self.hs = {"f64": [sfmm.Handle(P_max, "f64") for _ in self.streams],
+                   "f32": [sfmm.Handle(self.P32, "f32") for _ in self.streams]}
+        self.h = {k: v[0] for k, v in self.hs.items()}
+        self._sidx = {id(s): i for i, s in enumerate(self.streams)}
         self.chunk = chunk
         self.inflight = inflight_per_stream
         self.arena = Arena(arena_bytes, self.device)
@@ -182,7 +187,7 @@ class TranslationServer:
         a = r._next
         b = min(r.count, a + self.chunk)
         r._next = b
-        h = self.h["f64" if r._w == 8 else "f32"]
+        h = self.hs["f64" if r._w == 8 else "f32"][self._sidx[id(stream)]]
         n = b - a
         stream.wait_event(r._ready)
         sfmm.translate_batch(r.op, h, r._pin[a:b], r._pout[a:b], r._sh[a:b], r.p_in, r.p_out,
@@ -266,8 +271,9 @@ class TranslationServer:
         return self.run([r2], keep_outputs=True)[0]
 
     def close(self):
-        for h in self.h.values():
-            h.close()
+        for hl in self.hs.values():
+            for h in hl:
+                h.close()
 
 
 def make_requests(n, seed=5, P_lo=3, P_hi=30, count_lo=1e3, count_hi=1e6, pool_size=4096,

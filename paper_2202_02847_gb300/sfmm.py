@@ -180,19 +180,22 @@ def translate_lists(h, op, src, shift, offsets, out, p_in, p_out, n_targets,
 class ListClass(ctypes.Structure):
     """sfmm_list_class: one (op, p_in, p_out) class of a multi-class lists call."""
     _fields_ = [("op", ctypes.c_int), ("p_in", ctypes.c_int), ("p_out", ctypes.c_int),
-                ("reserved", ctypes.c_int), ("target_begin", ctypes.c_longlong),
+                ("lanes_per_target", ctypes.c_int), ("target_begin", ctypes.c_longlong),
                 ("target_end", ctypes.c_longlong)]
 
 
-MAX_CLASSES = 64
+MAX_CLASSES = 256
 POLICY = {"auto": 0, "unrolled": 1, "shared": 2, "global": 3}
 
 
 def translate_lists_multi(h, classes, src, shift, offsets, out, accumulate=False, stream=None):
-    """sfmm_translate_lists_multi: classes = [(op, p_in, p_out, target_begin, target_end)]."""
+    """sfmm_translate_lists_multi: classes = [(op, p_in, p_out, target_begin,
+    target_end[, lanes_per_target])] (lanes_per_target 0 = the default)."""
     arr = (ListClass * len(classes))()
-    for k, (op, pi, po, tb, te) in enumerate(classes):
-        arr[k] = ListClass(OPS.get(op, op), int(pi), int(po), 0, int(tb), int(te))
+    for k, cl in enumerate(classes):
+        op, pi, po, tb, te = cl[:5]
+        lanes = int(cl[5]) if len(cl) > 5 else 0
+        arr[k] = ListClass(OPS.get(op, op), int(pi), int(po), lanes, int(tb), int(te))
     _check(_lib.sfmm_translate_lists_multi(h.ptr, ctypes.cast(arr, _vp), len(classes), _addr(src),
                                            _addr(shift), _addr(offsets), _addr(out),
                                            int(bool(accumulate)), _stream(stream)),

@@ -295,3 +295,63 @@ def test_host_errors(sf, h64):
     with pytest.raises(sf.SfmmError) as e:
         sf.m2l_batch(h64, 0, 0, 0, 4, 4, 5)
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 8, 32])
+def test_lists_multi_lanes_per_target(sf, orc, h64, lanes):
+    """Two mixed-order M2L classes and one M2M class in one launch, lists of
+    0..70 sources, each class spread over `lanes` lanes per target (1: one
+    thread walks the list); every variant agrees with the oracle's sums, and
+    a second run gives bitwise the same result."""
+    import torch
+    g = W.rng(6100 + lanes)
+    spec = [("m2l", 9, 7, 40), ("m2l", 5, 11, 33), ("m2m", 8, 8, 21)]
+    nt = sum(c[3] for c in spec)
+    lens = g.integers(0, 71, size=nt)
+    lens[5] = 0
+    offs = np.zeros(nt + 1, np.int64)
+    np.cumsum(lens, out=offs[1:])
+    pmax = 11
+    S = pmax * (pmax + 1)
+    nsrc = 64
+    src_solids = {p: W.random_solids(g, nsrc, p) for p in (5, 8, 9)}
+    dS = {p: torch.tensor(v, device="cuda") for p, v in src_solids.items()}
+    dO = torch.zeros(nt, S, dtype=torch.float64, device="cuda")
+    ptrs = torch.zeros(int(offs[-1]), dtype=torch.int64)
+    shifts = W.shifts(g, int(offs[-1]))
+    classes, t0, want, picks = [], 0, [], []
+    for op, pi, po, n in spec:
+        for t in range(t0, t0 + n):
+            idx = g.integers(0, nsrc, size=lens[t])
+            picks.append(idx)
+            ptrs[offs[t]:offs[t + 1]] = sf.pointer_array(dS[pi], pi * (pi + 1), torch.tensor(idx)).cpu()
+        classes.append((op, pi, po, t0, t0 + n, lanes))
+        t0 += n
+    pout = torch.tensor([dO.data_ptr() + 8 * S * t for t in range(nt)], dtype=torch.int64, device="cuda")
+    args = (ptrs.cuda(), torch.tensor(shifts, device="cuda"), torch.tensor(offs, device="cuda"), pout)
+    sf.translate_lists_multi(h64, classes, *args)
+    torch.cuda.synchronize()
+    assert h64.sync_status() == 0
+    first = dO.clone()
+    sf.translate_lists_multi(h64, classes, *args)
+    torch.cuda.synchronize()
+    assert torch.equal(first, dO)
+    got = dO.cpu().numpy()
+    t = 0
+    for op, pi, po, n in spec:
+        for _ in range(n):
+            w = np.zeros(po * (po + 1))
+            for k, j in enumerate(range(offs[t], offs[t + 1])):
+                w += orc.translate(op, pi, po, src_solids[pi][picks[t][k]], shifts[j])
+            if lens[t] == 0:
+                assert not got[t].any(), t          # an empty list gives zeros
+            else:
+                assert U.rel_err(got[t, :po * (po + 1)], w, po, U.out_kind(op)) <= TOL["f64"], (op, t)
+            t += 1
+
+
+def test_lists_multi_rejects_bad_lanes(sf, h64):
+    import torch
+    z = torch.zeros(2, dtype=torch.int64, device="cuda")
+    with pytest.raises(sf.SfmmError):
+        sf.translate_lists_multi(h64, [("m2l", 4, 4, 0, 1, 3)], z, z, z, z)
