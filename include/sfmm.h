@@ -220,7 +220,7 @@ sfmm_status sfmm_set_policy(sfmm_handle h, sfmm_op op, int p_in, int p_out,
 
 /*
  * Allocate (or grow) the handle's global scratch so that the global-scratch
- * variants can serve orders up to p_in_max with four resident warps per SM:
+ * variants can serve orders up to p_in_max with eight resident warps per SM:
  * 2 p_in_max (p_in_max + 1) reals per lane, a rotated solid and a partial
  * output sum (sfmm_create reserves it for P_max).  Synchronous; not to be
  * called while work using the handle is in flight.  Errors: SFMM_ERR_ARG,

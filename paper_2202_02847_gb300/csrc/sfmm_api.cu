@@ -434,9 +434,10 @@ sfmm_status sfmm_create(int P_max, sfmm_dtype dtype, sfmm_handle *out) {
     if (st == SFMM_OK) {
         const size_t esz = dtype == SFMM_F64 ? sizeof(double) : sizeof(float);
         {
-            // four resident warps per SM; a lane's slot holds a rotated solid and
-            // an output solid of order P_max (the group-lists kernels use both)
-            h->scratch_bytes = (size_t)smc * 4 * WARP * 2 * x_elems(P_max) * esz;
+            // eight resident warps per SM (two per sub-partition); a lane's slot
+            // holds a rotated solid and an output solid of order P_max (the
+            // group-lists kernels use both)
+            h->scratch_bytes = (size_t)smc * 8 * WARP * 2 * x_elems(P_max) * esz;
             if (cudaMalloc(&h->d_scratch, h->scratch_bytes) != cudaSuccess) st = SFMM_ERR_NOMEM;
             else if (cudaEventCreateWithFlags(&h->scratch_free, cudaEventDisableTiming) != cudaSuccess)
                 st = SFMM_ERR_CUDA;
@@ -581,7 +582,7 @@ sfmm_status sfmm_reserve_scratch(sfmm_handle h, int p_in_max) {
     if (h == nullptr) return SFMM_ERR_ARG;
     if (p_in_max < 1 || p_in_max > h->Pmax) return SFMM_ERR_ORDER;
     const size_t sz = h->dtype == SFMM_F64 ? sizeof(double) : sizeof(float);
-    const size_t need = (size_t)h->sm_count * 4 * WARP * 2 * x_elems(p_in_max) * sz;
+    const size_t need = (size_t)h->sm_count * 8 * WARP * 2 * x_elems(p_in_max) * sz;
     std::lock_guard<std::mutex> lk(h->scratch_mu);
     if (h->d_scratch != nullptr && h->scratch_bytes >= need) return SFMM_OK;
     if (cudaDeviceSynchronize() != cudaSuccess) return SFMM_ERR_CUDA;

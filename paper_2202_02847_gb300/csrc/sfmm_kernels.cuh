@@ -33,10 +33,17 @@ enum { STATUS_NULL_POINTER = 1, STATUS_BAD_OFFSETS = 2 };
 constexpr int WARP = 32;
 
 // per-thread working set in elements for (p_in, p_out): the rotated solid
-// (x_elems) and the row buffers with the rotation powers (row_elems)
+// (x_elems) and two complex row buffers, plus for orders up to PTAB_MAX the
+// powers of e^{i alpha} and e^{i beta} (row_elems).  Above PTAB_MAX the
+// powers are regenerated per row: the tables would cost the shared memory of
+// half the resident warps, the regeneration ~4 FLOP per element and row.
+constexpr int PTAB_MAX = 12;
+__host__ __device__ inline bool power_tables(int p_in, int p_out) {
+    return (p_in > p_out ? p_in : p_out) <= PTAB_MAX;
+}
 __host__ __device__ inline int x_elems(int p_in) { return p_in * (p_in + 1); }
 __host__ __device__ inline int row_elems(int p_in, int p_out) {
-    return 8 * (p_in > p_out ? p_in : p_out);
+    return (power_tables(p_in, p_out) ? 8 : 4) * (p_in > p_out ? p_in : p_out);
 }
 
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
@@ -161,6 +168,27 @@ __device__ __forceinline__ void ztrans_block(const T *__restrict__ Tz, int Pm, i
     for (int j = 0; j < G; ++j) { Are[m0 + j] = ar[j]; Aim[m0 + j] = ai[j]; }
 }
 
+// Powers e^{i m theta}, m = 0, 1, 2, ... in that order, from two interleaved
+// recurrences (even and odd m, each stepping by e^{2 i theta}), so that
+// consecutive powers do not wait on each other and need no storage.
+template <typename T>
+struct PowSeq {
+    T er, ei, od_r, od_i, c2, s2;
+    __device__ __forceinline__ PowSeq(T c, T s)
+        : er(T(1)), ei(T(0)), od_r(c), od_i(s), c2(c * c - s * s), s2(T(2) * c * s) {}
+    __device__ __forceinline__ void next(int m, T &pr, T &pi) {
+        if (m & 1) {
+            pr = od_r; pi = od_i;
+            const T r = od_r * c2 - od_i * s2, i = fma_t(od_r, s2, od_i * c2);
+            od_r = r; od_i = i;
+        } else {
+            pr = er; pi = ei;
+            const T r = er * c2 - ei * s2, i = fma_t(er, s2, ei * c2);
+            er = r; ei = i;
+        }
+    }
+};
+
 // Output sink: overwrite or add one coefficient of the result (a solid in
 // memory, or a lane's interleaved slot in the scratch).
 template <typename T>
@@ -177,19 +205,22 @@ __device__ __forceinline__ void put(LaneArr<T> dst, T v, bool add) {
 // One translation computed by the calling thread (Sec. 3.4 steps 1-4, with
 // the z-axis translation of the op).  `buf` is this lane's shared memory of
 // lane_elems(p_in, p_out) elements.  add = accumulate into dst.
-template <typename T, int OP, typename D>
-__device__ void translate_one(const DevTables<T> &tb, int p_in, int p_out,
-                              const T *__restrict__ src, const T *__restrict__ shift,
-                              D dst, bool add, LaneArr<T> X, LaneArr<T> buf) {
+template <typename T, int OP, bool PT, typename D>
+__device__ void translate_impl(const DevTables<T> &tb, int p_in, int p_out,
+                               const T *__restrict__ src, const T *__restrict__ shift,
+                               D dst, bool add, LaneArr<T> X, LaneArr<T> buf) {
     const int P = p_in > p_out ? p_in : p_out;
     // lane memory map: X = rotated solid (rows k < p_in, p_in(p_in+1) elements),
-    // buf = two row buffers and the powers of e^{i alpha}, e^{i beta} (8P)
+    // buf = two complex row buffers (4P), then for P <= PTAB_MAX the powers of
+    // e^{i alpha} and e^{i beta} (4P); above, the powers are regenerated per
+    // row (PowSeq)
     const int xhalf = p_in * (p_in + 1) / 2;
     LaneArr<T> Xre = X, Xim = X + xhalf;
     LaneArr<T> Are = buf, Aim = Are + P;                     // row buffer A
     LaneArr<T> Bre = Aim + P, Bim = Bre + P;                 // row buffer B
-    LaneArr<T> PAre = Bim + P, PAim = PAre + P;              // e^{i m alpha}
-    LaneArr<T> PBre = PAim + P, PBim = PBre + P;             // e^{i m beta}
+    constexpr bool ptab = PT;                                // == power_tables(p_in, p_out)
+    LaneArr<T> PAre = Bim + P, PAim = PAre + P;              // e^{i m alpha} (ptab)
+    LaneArr<T> PBre = PAim + P, PBim = PBre + P;             // e^{i m beta} (ptab)
 
     // --- step 1: shift geometry without trigonometric functions (Sec. 3.4)
     const T x = shift[0], y = shift[1], z = shift[2];
@@ -209,7 +240,7 @@ __device__ void translate_one(const DevTables<T> &tb, int p_in, int p_out,
     if (rho > T(0)) { const T ir = T(1) / rho; ca = y * ir; sa = x * ir; }
     const T iR = T(1) / R;
     const T cb = z * iR, sb = -rho * iR;        // cos(beta) = z/|r|, sin(beta) = -rho/|r|
-    {
+    if constexpr (ptab) {
         T ar = T(1), ai = T(0), br = T(1), bi = T(0);
         for (int m = 0; m < P; ++m) {
             PAre[m] = ar; PAim[m] = ai; PBre[m] = br; PBim[m] = bi;
@@ -228,18 +259,24 @@ __device__ void translate_one(const DevTables<T> &tb, int p_in, int p_out,
         const T *row = src + n * (n + 1);
         const T *cf = ((OP == OP_L2L) ? tb.ic : tb.c) + n * (n + 1) / 2;
         // (b) scale, change to the orthonormal basis, rotate by alpha
+        PowSeq<T> pa(ca, sa);
         for (int m = 0; m <= n; ++m) {
             const T f = s * ldt(cf + m);
             const T re = row[m] * f, im = row[n + 1 + m] * f;
-            const T pr = PAre[m], pi = PAim[m];
+            T pr, pi;
+            if constexpr (ptab) { pr = PAre[m]; pi = PAim[m]; } else { pa.next(m, pr, pi); }
             Are[m] = re * pr - im * pi;
             Aim[m] = fma_t(re, pi, im * pr);
         }
         // (c) swap x and z
         swap_row(tb, n, Are, Aim, Bre, Bim, n + 1);
         // (d) rotate by beta
+        PowSeq<T> pb(cb, sb);
+        T pr, pi;
+        pb.next(0, pr, pi);
         for (int m = 1; m <= n; ++m) {
-            const T re = Bre[m], im = Bim[m], pr = PBre[m], pi = PBim[m];
+            if constexpr (ptab) { pr = PBre[m]; pi = PBim[m]; } else { pb.next(m, pr, pi); }
+            const T re = Bre[m], im = Bim[m];
             Bre[m] = re * pr - im * pi;
             Bim[m] = fma_t(re, pi, im * pr);
         }
@@ -263,24 +300,43 @@ __device__ void translate_one(const DevTables<T> &tb, int p_in, int p_out,
         if (m0 <= n) ztrans_block<T, OP, 1>(Tz, Pm, n, m0, p_in, Xre, Xim, Are, Aim);
         // swap, rotate by -beta, swap
         swap_row(tb, n, Are, Aim, Bre, Bim, n + 1);
-        for (int m = 1; m <= n; ++m) {
-            const T re = Bre[m], im = Bim[m], pr = PBre[m], pi = PBim[m];
-            Bre[m] = fma_t(re, pr, im * pi);
-            Bim[m] = im * pr - re * pi;
+        {
+            PowSeq<T> pb(cb, sb);
+            T pr, pi;
+            pb.next(0, pr, pi);
+            for (int m = 1; m <= n; ++m) {
+                if constexpr (ptab) { pr = PBre[m]; pi = PBim[m]; } else { pb.next(m, pr, pi); }
+                const T re = Bre[m], im = Bim[m];
+                Bre[m] = fma_t(re, pr, im * pi);
+                Bim[m] = im * pr - re * pi;
+            }
         }
         swap_row(tb, n, Bre, Bim, Are, Aim, n + 1);
         // rotate by -alpha, undo the scaling and the basis change, store
         const T *cf = ((OP == OP_M2M) ? tb.ic : tb.c) + n * (n + 1) / 2;
         D orow = dst + n * (n + 1);
+        PowSeq<T> pa(ca, sa);
         for (int m = 0; m <= n; ++m) {
             const T f = so * ldt(cf + m);
             const T re = Are[m] * f, im = Aim[m] * f;
-            const T pr = PAre[m], pi = PAim[m];
+            T pr, pi;
+            if constexpr (ptab) { pr = PAre[m]; pi = PAim[m]; } else { pa.next(m, pr, pi); }
             put(orow + m, fma_t(re, pr, im * pi), add);
             put(orow + n + 1 + m, im * pr - re * pi, add);
         }
         so *= step_out;
     }
+}
+
+// Dispatch on the storage of the rotation powers (compile-time in the loops).
+template <typename T, int OP, typename D>
+__device__ __forceinline__ void translate_one(const DevTables<T> &tb, int p_in, int p_out,
+                                              const T *__restrict__ src, const T *__restrict__ shift,
+                                              D dst, bool add, LaneArr<T> X, LaneArr<T> buf) {
+    if (power_tables(p_in, p_out))
+        translate_impl<T, OP, true>(tb, p_in, p_out, src, shift, dst, add, X, buf);
+    else
+        translate_impl<T, OP, false>(tb, p_in, p_out, src, shift, dst, add, X, buf);
 }
 
 // ---------------------------------------------------------------- kernels
