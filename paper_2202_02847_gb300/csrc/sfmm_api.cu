@@ -8,6 +8,7 @@
 
 #include "sfmm.h"
 #include "sfmm_ctx.h"
+#include "sfmm_generic.h"
 #include "sfmm_kernels.cuh"
 #include "sfmm_tables.h"
 #include "sfmm_unrolled.cuh"
@@ -23,24 +24,12 @@ namespace {
 constexpr int kMaxPmax64 = 64;
 constexpr int kMaxPmax32 = 29;
 
-template <typename T, bool XG>
-void set_attrs_one(size_t smem) {
-    cudaFuncSetAttribute(batch_kernel<T, OP_M2M, XG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(batch_kernel<T, OP_M2L, XG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(batch_kernel<T, OP_L2L, XG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(lists_kernel<T, OP_M2M, XG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(lists_kernel<T, OP_M2L, XG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(lists_kernel<T, OP_L2L, XG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
 template <typename T>
 void set_kernel_attrs(size_t smem) {
-    set_attrs_one<T, false>(smem);
-    set_attrs_one<T, true>(smem);
-    cudaFuncSetAttribute(multi_lists_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(glists_kernel<T, OP_M2M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(glists_kernel<T, OP_M2L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(glists_kernel<T, OP_L2L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_generic_attrs<T, OP_M2M>(smem);
+    set_generic_attrs<T, OP_M2L>(smem);
+    set_generic_attrs<T, OP_L2L>(smem);
+    set_multi_attrs<T>(smem);
     cudaFuncSetAttribute(p2x_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(p2x_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
@@ -132,12 +121,6 @@ sfmm_status check_common(sfmm_handle h, int p_in, int p_out, long long count) {
 }
 
 // Launch geometry of one translation call.
-struct Geometry {
-    bool xg = false;        // rotated solid in global scratch
-    int warps = 0;          // warps per block
-    size_t smem = 0;        // dynamic shared memory per block
-    long long blocks = 0;
-};
 
 template <typename T>
 bool shared_only_fits(const sfmm_ctx *h, int p_in, int p_out) {
@@ -213,42 +196,6 @@ struct ScratchGuard {
     }
 };
 
-// Persistent grid: no more blocks than the device holds at once.
-template <typename K>
-long long resident_blocks(const sfmm_ctx *h, K kernel, const Geometry &g) {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, g.warps * WARP, g.smem) != cudaSuccess || nb < 1)
-        nb = 1;
-    long long cap = (long long)nb * h->sm_count;
-    return g.blocks < cap ? g.blocks : cap;
-}
-
-template <typename T, int OP>
-void batch_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
-                  const T *const *I, T *const *O, const T *S, int p_in, int p_out,
-                  long long count, int acc, T *scratch, int *status) {
-    if (g.xg) {
-        auto k = batch_kernel<T, OP, true>;
-        k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, I, O, S, p_in, p_out, count, acc, scratch, status);
-    } else {
-        auto k = batch_kernel<T, OP, false>;
-        k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, I, O, S, p_in, p_out, count, acc, scratch, status);
-    }
-}
-
-template <typename T, int OP>
-void lists_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
-                  const T *const *Sp, const T *S, const long long *offsets, T *const *O,
-                  int p_in, int p_out, long long nt, int acc, T *scratch, int *status) {
-    if (g.xg) {
-        auto k = lists_kernel<T, OP, true>;
-        k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, Sp, S, offsets, O, p_in, p_out, nt, acc, scratch, status);
-    } else {
-        auto k = lists_kernel<T, OP, false>;
-        k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, Sp, S, offsets, O, p_in, p_out, nt, acc, scratch, status);
-    }
-}
-
 template <typename T>
 sfmm_status launch_batch(sfmm_handle h, int op, const void *const *in, void *const *out,
                          const void *shift, int p_in, int p_out, long long count,
@@ -298,14 +245,6 @@ Geometry group_geometry(const sfmm_ctx *h, int op, int p_in, int p_out, long lon
     g.smem = (size_t)w * per_warp;
     g.blocks = blocks;
     return g;
-}
-
-template <typename T, int OP>
-void glists_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
-                   const T *const *Sp, const T *S, const long long *offsets, T *const *O,
-                   int p_in, int p_out, long long nt, int acc, int G, T *scratch, int *status) {
-    auto k = glists_kernel<T, OP>;
-    k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, Sp, S, offsets, O, p_in, p_out, nt, acc, G, scratch, status);
 }
 
 template <typename T>
@@ -642,15 +581,16 @@ static sfmm_status launch_multi(sfmm_handle h, const sfmm_list_class *classes, i
     long long blocks = slots / w;
     const long long need = (chunks + w - 1) / w;
     if (blocks > need) blocks = need;
-    auto k = multi_lists_kernel<T>;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, w * WARP, (size_t)w * per_warp) == cudaSuccess &&
-        nb > 0 && blocks > (long long)nb * h->sm_count)
-        blocks = (long long)nb * h->sm_count;
+    if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
+    Geometry g;
+    g.xg = true;
+    g.warps = w;
+    g.smem = (size_t)w * per_warp;
+    g.blocks = blocks;
     ScratchGuard guard(h, stream, true);
-    k<<<(unsigned)blocks, w * WARP, (size_t)w * per_warp, stream>>>(
-        tb, mp, reinterpret_cast<const T *const *>(src), reinterpret_cast<const T *>(shift), offsets,
-        reinterpret_cast<T *const *>(out), accumulate, reinterpret_cast<T *>(h->d_scratch), h->d_status);
+    multi_launch<T>(h, g, stream, tb, mp, reinterpret_cast<const T *const *>(src), reinterpret_cast<const T *>(shift),
+                    offsets, reinterpret_cast<T *const *>(out), accumulate, reinterpret_cast<T *>(h->d_scratch),
+                    h->d_status);
     return cudaGetLastError() == cudaSuccess ? SFMM_OK : SFMM_ERR_CUDA;
 }
 

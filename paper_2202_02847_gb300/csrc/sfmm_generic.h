@@ -1,0 +1,52 @@
+// Launches of the generic (runtime-order) translation kernels.  The kernels
+// are heavy to compile, so each (real type, op) and the multi-class kernel of
+// each real type live in a translation unit of their own
+// (sfmm_generic_<type>_<op>.cu, sfmm_generic_<type>_multi.cu, all including
+// sfmm_generic_inst.cuh); the handle code calls them through these
+// declarations.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+#include "sfmm_ctx.h"
+#include "sfmm_kernels.cuh"
+
+namespace sfmm {
+
+// launch shape of a generic kernel
+struct Geometry {
+    bool xg = false;        // rotated solid in global scratch
+    int warps = 0;          // warps per block
+    size_t smem = 0;        // dynamic shared memory per block
+    long long blocks = 0;   // upper bound; the launch caps it at the resident capacity
+};
+
+template <typename T, int OP>
+void batch_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
+                  const T *const *I, T *const *O, const T *S, int p_in, int p_out,
+                  long long count, int acc, T *scratch, int *status);
+
+template <typename T, int OP>
+void lists_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
+                  const T *const *Sp, const T *S, const long long *offsets, T *const *O,
+                  int p_in, int p_out, long long nt, int acc, T *scratch, int *status);
+
+template <typename T, int OP>
+void glists_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
+                   const T *const *Sp, const T *S, const long long *offsets, T *const *O,
+                   int p_in, int p_out, long long nt, int acc, int G, T *scratch, int *status);
+
+template <typename T>
+void multi_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
+                  const MultiParams &mp, const T *const *src, const T *shift, const long long *offsets,
+                  T *const *out, int acc, T *scratch, int *status);
+
+// raise the dynamic shared memory limit of the kernels of one unit
+template <typename T, int OP>
+void set_generic_attrs(size_t smem);
+template <typename T>
+void set_multi_attrs(size_t smem);
+
+}  // namespace sfmm

@@ -1,0 +1,4 @@
+// Generic L2L kernels for float (see sfmm_generic.h).
+#define SFMM_GENERIC_T float
+#define SFMM_GENERIC_OP sfmm::OP_L2L
+#include "sfmm_generic_inst.cuh"

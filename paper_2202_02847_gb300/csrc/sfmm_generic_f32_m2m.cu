@@ -1,0 +1,4 @@
+// Generic M2M kernels for float (see sfmm_generic.h).
+#define SFMM_GENERIC_T float
+#define SFMM_GENERIC_OP sfmm::OP_M2M
+#include "sfmm_generic_inst.cuh"

@@ -1,0 +1,108 @@
+// Definitions of the generic launches, explicitly instantiated for one real
+// type (SFMM_GENERIC_T) and either one op (SFMM_GENERIC_OP) or the
+// multi-class kernel (SFMM_GENERIC_MULTI).  Included by one small translation
+// unit per case, so the units compile in parallel.
+#include "sfmm_generic.h"
+
+#if !defined(SFMM_GENERIC_T) || !(defined(SFMM_GENERIC_OP) || defined(SFMM_GENERIC_MULTI))
+#error "define SFMM_GENERIC_T and SFMM_GENERIC_OP or SFMM_GENERIC_MULTI before including this file"
+#endif
+
+namespace sfmm {
+namespace {
+
+// Persistent grid: no more blocks than the device holds at once.
+template <typename K>
+long long resident_blocks(const sfmm_ctx *h, K kernel, const Geometry &g) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, g.warps * WARP, g.smem) != cudaSuccess || nb < 1)
+        nb = 1;
+    long long cap = (long long)nb * h->sm_count;
+    return g.blocks < cap ? g.blocks : cap;
+}
+
+template <typename K>
+void attr(K k, size_t smem) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace
+
+template <typename T, int OP>
+void batch_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
+                  const T *const *I, T *const *O, const T *S, int p_in, int p_out,
+                  long long count, int acc, T *scratch, int *status) {
+    if (g.xg) {
+        auto k = batch_kernel<T, OP, true>;
+        k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, I, O, S, p_in, p_out, count, acc, scratch, status);
+    } else {
+        auto k = batch_kernel<T, OP, false>;
+        k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, I, O, S, p_in, p_out, count, acc, scratch, status);
+    }
+}
+
+template <typename T, int OP>
+void lists_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
+                  const T *const *Sp, const T *S, const long long *offsets, T *const *O,
+                  int p_in, int p_out, long long nt, int acc, T *scratch, int *status) {
+    if (g.xg) {
+        auto k = lists_kernel<T, OP, true>;
+        k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, Sp, S, offsets, O, p_in, p_out, nt, acc, scratch, status);
+    } else {
+        auto k = lists_kernel<T, OP, false>;
+        k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, Sp, S, offsets, O, p_in, p_out, nt, acc, scratch, status);
+    }
+}
+
+template <typename T, int OP>
+void glists_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
+                   const T *const *Sp, const T *S, const long long *offsets, T *const *O,
+                   int p_in, int p_out, long long nt, int acc, int G, T *scratch, int *status) {
+    auto k = glists_kernel<T, OP>;
+    k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, Sp, S, offsets, O, p_in, p_out, nt, acc, G, scratch, status);
+}
+
+template <typename T>
+void multi_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
+                  const MultiParams &mp, const T *const *src, const T *shift, const long long *offsets,
+                  T *const *out, int acc, T *scratch, int *status) {
+    auto k = multi_lists_kernel<T>;
+    k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, mp, src, shift, offsets, out, acc, scratch, status);
+}
+
+template <typename T, int OP>
+void set_generic_attrs(size_t smem) {
+    attr(batch_kernel<T, OP, false>, smem);
+    attr(batch_kernel<T, OP, true>, smem);
+    attr(lists_kernel<T, OP, false>, smem);
+    attr(lists_kernel<T, OP, true>, smem);
+    attr(glists_kernel<T, OP>, smem);
+}
+
+template <typename T>
+void set_multi_attrs(size_t smem) {
+    attr(multi_lists_kernel<T>, smem);
+}
+
+#if defined(SFMM_GENERIC_OP)
+using GT = SFMM_GENERIC_T;
+constexpr int GOP = SFMM_GENERIC_OP;
+template void batch_launch<GT, GOP>(const sfmm_ctx *, const Geometry &, cudaStream_t, const DevTables<GT> &,
+                                    const GT *const *, GT *const *, const GT *, int, int, long long, int,
+                                    GT *, int *);
+template void lists_launch<GT, GOP>(const sfmm_ctx *, const Geometry &, cudaStream_t, const DevTables<GT> &,
+                                    const GT *const *, const GT *, const long long *, GT *const *, int, int,
+                                    long long, int, GT *, int *);
+template void glists_launch<GT, GOP>(const sfmm_ctx *, const Geometry &, cudaStream_t, const DevTables<GT> &,
+                                     const GT *const *, const GT *, const long long *, GT *const *, int, int,
+                                     long long, int, int, GT *, int *);
+template void set_generic_attrs<GT, GOP>(size_t);
+#else
+using GT = SFMM_GENERIC_T;
+template void multi_launch<GT>(const sfmm_ctx *, const Geometry &, cudaStream_t, const DevTables<GT> &,
+                               const MultiParams &, const GT *const *, const GT *, const long long *,
+                               GT *const *, int, GT *, int *);
+template void set_multi_attrs<GT>(size_t);
+#endif
+
+}  // namespace sfmm

@@ -329,12 +329,15 @@ __device__ void translate_impl(const DevTables<T> &tb, int p_in, int p_out,
 }
 
 // Dispatch on the storage of the rotation powers (compile-time in the loops).
-template <typename T, int OP, typename D>
+// TABLES = false always regenerates them (one code path: the multi-class
+// kernel, which serves all three ops, keeps its compile time down that way;
+// its row buffers are still sized by row_elems).
+template <typename T, int OP, bool TABLES = true, typename D>
 __device__ __forceinline__ void translate_one(const DevTables<T> &tb, int p_in, int p_out,
                                               const T *__restrict__ src, const T *__restrict__ shift,
                                               D dst, bool add, LaneArr<T> X, LaneArr<T> buf) {
-    if (power_tables(p_in, p_out))
-        translate_impl<T, OP, true>(tb, p_in, p_out, src, shift, dst, add, X, buf);
+    if (TABLES && power_tables(p_in, p_out))
+        translate_impl<T, OP, TABLES>(tb, p_in, p_out, src, shift, dst, add, X, buf);
     else
         translate_impl<T, OP, false>(tb, p_in, p_out, src, shift, dst, add, X, buf);
 }
@@ -424,7 +427,7 @@ __global__ void __launch_bounds__(256, 1) lists_kernel(DevTables<T> tb, const T 
 // member mem adds the coefficients mem, mem + G, ... of the group's slots, in
 // lane order, into the target.  The order of the additions is fixed, so the
 // result does not depend on timing.
-template <typename T, int OP>
+template <typename T, int OP, bool TABLES = true>
 __device__ void group_chunk(const DevTables<T> &tb, int p_in, int p_out, int G, long long t,
                             long long t_end, const T *const *src, const T *shift,
                             const long long *offsets, T *const *out, int accumulate,
@@ -446,7 +449,7 @@ __device__ void group_chunk(const DevTables<T> &tb, int p_in, int p_out, int G, 
     for (long long j = j0 + mem; j < j1; j += G) {
         const T *s = src[j];
         if (s == nullptr) { atomicOr(status, STATUS_NULL_POINTER); continue; }
-        translate_one<T, OP>(tb, p_in, p_out, s, shift + 3 * j, Y, any, X, buf);
+        translate_one<T, OP, TABLES>(tb, p_in, p_out, s, shift + 3 * j, Y, any, X, buf);
         any = true;
     }
     const unsigned has = __ballot_sync(0xffffffffu, any);
@@ -529,11 +532,11 @@ __global__ void __launch_bounds__(256, 1) multi_lists_kernel(DevTables<T> tb, Mu
             const long long tg = cl.tb + (c - cl.chunk_begin) * (WARP / cl.g) + lane / cl.g;
             const LaneArr<T> Y = X + x_elems(cl.p_in);
             if (cl.op == OP_M2M)
-                group_chunk<T, OP_M2M>(tb, cl.p_in, cl.p_out, cl.g, tg, cl.te, src, shift, offsets, out, accumulate, X, Y, buf, status);
+                group_chunk<T, OP_M2M, false>(tb, cl.p_in, cl.p_out, cl.g, tg, cl.te, src, shift, offsets, out, accumulate, X, Y, buf, status);
             else if (cl.op == OP_M2L)
-                group_chunk<T, OP_M2L>(tb, cl.p_in, cl.p_out, cl.g, tg, cl.te, src, shift, offsets, out, accumulate, X, Y, buf, status);
+                group_chunk<T, OP_M2L, false>(tb, cl.p_in, cl.p_out, cl.g, tg, cl.te, src, shift, offsets, out, accumulate, X, Y, buf, status);
             else
-                group_chunk<T, OP_L2L>(tb, cl.p_in, cl.p_out, cl.g, tg, cl.te, src, shift, offsets, out, accumulate, X, Y, buf, status);
+                group_chunk<T, OP_L2L, false>(tb, cl.p_in, cl.p_out, cl.g, tg, cl.te, src, shift, offsets, out, accumulate, X, Y, buf, status);
             continue;
         }
         const long long t = cl.tb + (c - cl.chunk_begin) * WARP + lane;
@@ -548,9 +551,9 @@ __global__ void __launch_bounds__(256, 1) multi_lists_kernel(DevTables<T> tb, Mu
         for (long long j = j0; j < j1; ++j) {
             const T *s = src[j];
             if (s == nullptr) { atomicOr(status, STATUS_NULL_POINTER); continue; }
-            if (cl.op == OP_M2M) translate_one<T, OP_M2M>(tb, cl.p_in, cl.p_out, s, shift + 3 * j, dst, add, X, buf);
-            else if (cl.op == OP_M2L) translate_one<T, OP_M2L>(tb, cl.p_in, cl.p_out, s, shift + 3 * j, dst, add, X, buf);
-            else translate_one<T, OP_L2L>(tb, cl.p_in, cl.p_out, s, shift + 3 * j, dst, add, X, buf);
+            if (cl.op == OP_M2M) translate_one<T, OP_M2M, false>(tb, cl.p_in, cl.p_out, s, shift + 3 * j, dst, add, X, buf);
+            else if (cl.op == OP_M2L) translate_one<T, OP_M2L, false>(tb, cl.p_in, cl.p_out, s, shift + 3 * j, dst, add, X, buf);
+            else translate_one<T, OP_L2L, false>(tb, cl.p_in, cl.p_out, s, shift + 3 * j, dst, add, X, buf);
             add = true;
         }
     }
