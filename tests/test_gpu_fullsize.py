@@ -1,0 +1,117 @@
+"""Full-size workloads in the launch configuration the benchmark times, checked
+on sampled outputs against the oracle (which forms every source multipole
+directly from the particles in the source box: P2M of a box's particles equals
+the M2M-combined multipoles of its children at the same order).
+
+* Uniform octree, level 5 (32^3 leaves, 2^20 uniform points, q ~ U[-1, 1],
+  seed 2), P = 10, FP64: the upward pass and the pass's single M2L lists launch
+  (levels 2-5) as the benchmark runs them; 10 sampled level-5 targets and 2
+  level-3 targets.  A second run of the same launches gives bitwise the same
+  locals (the lists kernels add in a fixed order).
+* The same tree at P = 16 through the tensor-core grid M2L of level 5
+  (3xTF32 products, FP64 target sums): 3 sampled targets at the FP32-class
+  tolerance."""
+import numpy as np
+import pytest
+
+from paper_2202_02847_gb300 import workloads as W
+import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+NPOINTS = 1 << 20
+DEPTH = 5
+
+
+@pytest.fixture(scope="module")
+def tree():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return W.uniform_octree(DEPTH, NPOINTS, seed=2)
+
+
+@pytest.fixture(scope="module")
+def sf():
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_2202_02847_gb300 import sfmm
+    return sfmm
+
+
+def _box_points(tree, level):
+    """Point indices of every box of a level (boxes of level l contain the
+    leaves whose index, read in octal digits, starts with the box's)."""
+    ijk = np.floor(tree.points * (1 << level)).astype(np.int64).clip(0, (1 << level) - 1)
+    box = W.box_index(ijk[:, 0], ijk[:, 1], ijk[:, 2], 1 << level)
+    order = np.argsort(box, kind="stable")
+    offs = np.concatenate([[0], np.cumsum(np.bincount(box, minlength=8 ** level))])
+    return order, offs
+
+
+def _oracle_m2l(orc, tree, level, t, P, cache):
+    lv = tree.levels[level]
+    if level not in cache:
+        cache[level] = _box_points(tree, level)
+    order, offs = cache[level]
+    want = np.zeros(P * (P + 1))
+    for j in range(lv.m2l_offsets[t], lv.m2l_offsets[t + 1]):
+        s = lv.m2l_sources[j]
+        sel = order[offs[s]:offs[s + 1]]
+        Ms = orc.p2m(P, tree.points[sel], tree.charges[sel], lv.centres[s])
+        want += orc.translate("m2l", P, P, Ms, lv.m2l_shift[j])
+    return want
+
+
+def test_octree_level5_p10_sampled_against_oracle(sf, orc, tree):
+    import torch
+    from paper_2202_02847_gb300.fmm import UniformPass
+    P = 10
+    h = sf.Handle(P, "f64")
+    fp = UniformPass(tree, P, h)
+    fp.p2m_leaves(tree.points, tree.charges, tree.leaf_of_point)
+    fp.upward()
+    fp.m2l_all()
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    L1 = fp.L.clone()
+    fp.upward()
+    fp.m2l_all()
+    torch.cuda.synchronize()
+    assert torch.equal(fp.L, L1)
+    L = L1.cpu().numpy()
+    g = W.rng(77)
+    cache = {}
+    for level, k in ((5, 10), (3, 2)):
+        for t in g.choice(8 ** level, size=k, replace=False):
+            want = _oracle_m2l(orc, tree, level, t, P, cache)
+            got = L[int(fp.level_base[level]) + t]
+            assert U.rel_err(got, want, P, "L") <= 1e-12, (level, t)
+    h.close()
+
+
+def test_grid_level5_p16_sampled_against_oracle(sf, orc, tree):
+    import torch
+    P = 16
+    h = sf.Handle(P, "f64")
+    lv = tree.levels[DEPTH]
+    nb = 8 ** DEPTH
+    order = np.argsort(tree.leaf_of_point, kind="stable")
+    offs = np.concatenate([[0], np.cumsum(np.bincount(tree.leaf_of_point, minlength=nb))])
+    M = torch.zeros(nb, P * (P + 1), dtype=torch.float64, device="cuda")
+    sf.p2m_boxes(h, P, torch.tensor(tree.points[order], device="cuda"),
+                 torch.tensor(tree.charges[order], device="cuda"), torch.tensor(offs, device="cuda"),
+                 torch.tensor(lv.centres, device="cuda"), M, nb)
+    grid = sf.Grid(h, P, 1 << DEPTH)
+    L = torch.zeros_like(M)
+    grid.m2l(lv.h, M, L)
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    got = L.cpu().numpy()
+    g = W.rng(78)
+    cache = {}
+    for t in g.choice(nb, size=3, replace=False):
+        want = _oracle_m2l(orc, tree, DEPTH, t, P, cache)
+        assert U.rel_err(got[t], want, P, "L") <= 1e-5, t
+    grid.close()
+    h.close()
