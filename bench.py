@@ -334,6 +334,11 @@ def run_precision(args):
     err = {"tensor_3xtf32": U.rel_err(L_tc.cpu().numpy(), ref, Pp, "L"),
            "rotation_fp32": U.rel_err(L32.double().cpu().numpy(), ref, Pp, "L"),
            "rotation_fp64": 0.0}
+    w = U.weights(Pp, "L")
+    per_target = {k: np.linalg.norm((a - ref) * w, axis=1) / np.linalg.norm(ref * w, axis=1)
+                  for k, a in (("tensor_3xtf32", L_tc.cpu().numpy()),
+                               ("rotation_fp32", L32.double().cpu().numpy()))}
+    err_max = {k: float(v.max()) for k, v in per_target.items()}
     ntr = int(lv.m2l_offsets[-1])
     dense_flop = 2 * (Pp * Pp) ** 2 * ntr                  # algorithmic, one dense product
     tf32_peak = 1917.3e12 * 1.1 / 2.25                      # measured bf16 x nominal tf32/bf16
@@ -359,6 +364,7 @@ def run_precision(args):
         "paths_ms": times,
         "paths_translations_per_s": {k: ntr / (v * 1e-3) for k, v in times.items()},
         "rel_err_vs_fp64_rotation": err,
+        "rel_err_max_target_vs_fp64_rotation": err_max,
         "gpu_launches": 3,
     }
     c = clk.summary()

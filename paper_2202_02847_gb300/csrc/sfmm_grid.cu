@@ -9,19 +9,21 @@
 //     x_k^m = M_k^m c_k^m / h^{k+1},   y_n^m = L_n^m h^n / c_n^m,   y = T_u x,
 // (eq. scaling with s = 1/h), and a target's local expansion is the sum of
 // T_u x over its 189 offsets.  Targets of the same child octant share the same
-// 189 offsets, so one CTA computes y for 64 targets of one octant as a GEMM
-// with K = 189 * 256 on the 5th-generation tensor cores:
+// 189 offsets, so a tile of 128 same-octant targets (64 when the grid side is
+// not a multiple of 16) is one GEMM with K = 189 * 256 on the 5th-generation
+// tensor cores:
 //   * T_u and x are split into TF32 hi + lo parts and multiplied as
 //     hi*hi + hi*lo + lo*hi (3xTF32, about 21 significant bits) with FP32
-//     accumulation in tensor memory (two 128-row halves x 64 columns);
-//   * every 8 offsets the accumulator is read out (tcgen05.ld) and added into
-//     an FP64 accumulator in global memory (the target's sum is FP64);
-//   * operand chunks (16 of K) are staged in shared memory in the canonical
-//     K-major layout in a four-stage pipeline: the T_u chunk is stored
-//     pre-tiled in global memory and arrives by one TMA bulk copy, the
-//     targets' source vectors are gathered by 16-byte cp.async copies;
-//   * a CTA holds 128 targets (64 on grids below 16^3), so every T_u chunk
-//     read from L2 serves 128 target columns.
+//     accumulation in tensor memory (two 128-row halves x 128 columns, two
+//     buffers);
+//   * every 2 offsets the accumulator is read out (tcgen05.ld) and added into
+//     the target's FP64 sum in global memory (FP32 rounding over longer runs
+//     of offsets pushed single targets above a 1e-5 relative error);
+//   * operand chunks (16 of K) are staged in shared memory in four stages: the
+//     T_u chunk, stored pre-tiled, by one bulk copy; the targets' source
+//     vectors, stored split by coordinate parity, by two 5-D tensor copies;
+//   * one thread issues copies, one issues MMAs, four warps drain the
+//     accumulators; one persistent CTA per SM.
 // T_u are built once per grid object with the FP64 rotation-based M2L on the
 // 256 basis vectors of every offset.  Every mbarrier wait is bounded: on
 // time-out the kernel records SFMM_GRID_TIMEOUT in the status word, stops
@@ -49,7 +51,7 @@ constexpr int KC = 16;             // K chunk staged in shared memory
 constexpr int NST = 4;             // pipeline stages
 constexpr int NKC = KD / KC;       // chunks per offset
 constexpr int A_PART = KD * KC * 4;   // one operand part (hi or lo) of an A chunk: 16 KB
-constexpr int FLUSH = 8;           // offsets accumulated in FP32 before an FP64 flush
+constexpr int FLUSH = 2;           // offsets accumulated in FP32 before an FP64 flush
 constexpr int NU = 189;            // offsets of a child octant
 constexpr int NCH_ALL = NU * NKC;  // K chunks of a tile
 constexpr int NCODE = 343;         // offset codes ((dx+3)*7 + dy+3)*7 + dz+3

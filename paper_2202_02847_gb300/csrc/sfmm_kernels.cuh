@@ -54,6 +54,15 @@ __device__ __forceinline__ float sqrt_t(float a) { return sqrtf(a); }
 template <typename T>
 __device__ __forceinline__ T ldt(const T *p) { return __ldg(p); }
 
+// Chunk of persistent warp w (of nw) in round k.  Rounds alternate direction,
+// so that with chunks ordered by decreasing cost (lists sorted by length) the
+// warps' totals, and the SMs' (whose warps are consecutive), stay within one
+// chunk of each other; round-robin in one direction gives the first warps the
+// largest chunk of every round.
+__device__ __forceinline__ long long deal_chunk(long long k, long long nw, long long w) {
+    return k * nw + ((k & 1) ? nw - 1 - w : w);
+}
+
 // Lane-strided view: element e lives at base[e * WARP].
 template <typename T>
 struct LaneArr {
@@ -366,9 +375,10 @@ struct LaneStore {
 };
 
 // Work distribution: the units (translations or targets) are cut into chunks
-// of 32, one per warp, handed out round-robin over a persistent grid sized to
-// the resident capacity.  Callers order units by decreasing cost, so the
-// round-robin deal balances the warps.
+// of 32 (or 32 / G targets), one per warp, dealt over a persistent grid sized
+// to the resident capacity: in order for translations (equal costs), in
+// alternating directions (deal_chunk) for lists, which callers sort by
+// decreasing length.
 template <typename T, int OP, bool XG>
 __global__ void __launch_bounds__(256, 1) batch_kernel(DevTables<T> tb, const T *const *in,
                                                     T *const *out, const T *shift, int p_in,
@@ -399,8 +409,9 @@ __global__ void __launch_bounds__(256, 1) lists_kernel(DevTables<T> tb, const T 
     LaneStore<T, XG> ls(reinterpret_cast<T *>(smem_raw), scratch, p_in, p_out);
     const int lane = threadIdx.x & (WARP - 1);
     const long long nw = (long long)gridDim.x * (blockDim.x / WARP);
-    for (long long c = (long long)blockIdx.x * (blockDim.x / WARP) + threadIdx.x / WARP;
-         c * WARP < n_targets; c += nw) {
+    const long long w = (long long)blockIdx.x * (blockDim.x / WARP) + threadIdx.x / WARP;
+    for (long long k = 0; k * nw * WARP < n_targets; ++k) {
+        const long long c = deal_chunk(k, nw, w);
         const long long t = c * WARP + lane;
         if (t >= n_targets) continue;
         T *dst = out[t];
@@ -484,9 +495,12 @@ __global__ void __launch_bounds__(256, 1) glists_kernel(DevTables<T> tb, const T
     LaneArr<T> buf{reinterpret_cast<T *>(smem_raw) + (size_t)warp * row_elems(p_in, p_out) * WARP + lane};
     const int ng = WARP / G;
     const long long nw = (long long)gridDim.x * (blockDim.x / WARP);
-    for (long long c = slot; c * ng < n_targets; c += nw)
+    for (long long k = 0; k * nw * ng < n_targets; ++k) {
+        const long long c = deal_chunk(k, nw, slot);
+        if (c * ng >= n_targets) continue;
         group_chunk<T, OP>(tb, p_in, p_out, G, c * ng + lane / G, n_targets, src, shift, offsets, out,
                            accumulate, X, Y, buf, status);
+    }
 }
 
 // Several classes of lists in one persistent launch.  The class table travels
@@ -521,7 +535,9 @@ __global__ void __launch_bounds__(256, 1) multi_lists_kernel(DevTables<T> tb, Mu
     LaneArr<T> X{scratch + slot * mp.x_slot * WARP + lane};
     LaneArr<T> buf{reinterpret_cast<T *>(smem_raw) + (size_t)warp * mp.row_slot * WARP + lane};
     const long long nw = (long long)gridDim.x * (blockDim.x / WARP);
-    for (long long c = slot; c < mp.total_chunks; c += nw) {
+    for (long long r = 0; r * nw < mp.total_chunks; ++r) {
+        const long long c = deal_chunk(r, nw, slot);
+        if (c >= mp.total_chunks) continue;
         int k = 0, hi = mp.n - 1;                     // last class with chunk_begin <= c
         while (k < hi) {
             const int mid = (k + hi + 1) >> 1;

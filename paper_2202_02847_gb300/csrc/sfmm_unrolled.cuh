@@ -338,7 +338,10 @@ __global__ void __launch_bounds__(256, 1) ulists_kernel(const T *const *src, con
     const int q = lane / G, mem = lane % G;
     Sw<T> X{reinterpret_cast<T *>(smem_raw) + (size_t)warp * S * XSTRIDE, lane};
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + warp; c * NG < n_targets; c += nw) {
+    const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    for (long long k = 0; k * nw * NG < n_targets; ++k) {
+        const long long c = deal_chunk(k, nw, w);
+        if (c * NG >= n_targets) continue;
         const long long t = c * NG + q;
         long long j0 = 0, j1 = 0;
         if (t < n_targets) {
