@@ -497,6 +497,12 @@ def run_serving(args):
     srv.run(reqs)
     cap_s = time.perf_counter() - t0
     cap_rps = len(reqs) / cap_s
+    # the plain form: the same requests one at a time, each finished before the
+    # next starts (no overlap on the device)
+    t0 = time.perf_counter()
+    for r in serve.make_requests(args.requests, seed=5):
+        srv.run([r])
+    ser_s = time.perf_counter() - t0
     loads = {}
     for load in (0.5, 0.8):
         rr = serve.poisson_arrivals(serve.make_requests(args.requests, seed=5), load * cap_rps,
@@ -521,6 +527,8 @@ def run_serving(args):
                    "arena_gb": 24},
         "capacity": {"requests_per_s": cap_rps, "translations_per_s": ntr / cap_s,
                      "gflop_per_s": flop / cap_s / 1e9, "seconds": cap_s},
+        "one_at_a_time": {"requests_per_s": len(reqs) / ser_s, "translations_per_s": ntr / ser_s,
+                          "seconds": ser_s},
         "latency": loads,
     }
     print(json.dumps(line))

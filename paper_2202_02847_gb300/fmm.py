@@ -264,7 +264,8 @@ class AdaptivePass:
         self.counts = dict(m2m=int(sum(len(d["src"]) for d in self.m2m)), m2l=self.n_m2l,
                            l2l=int(sum(d["count"] for d in self.l2l)))
         pmax = int(self.P.max())
-        sfmm.reserve_scratch(handle, pmax)
+        if handle is not None:                    # None: build the plan only (host tests)
+            sfmm.reserve_scratch(handle, pmax)
 
     # ------------------------------------------------------------ inputs
     def p2m_leaves(self, points, charges):

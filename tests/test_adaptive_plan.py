@@ -1,0 +1,52 @@
+"""Host logic of the adaptive pass: the M2L waves and their classes (CPU only)."""
+import numpy as np
+import pytest
+
+from paper_2202_02847_gb300 import workloads as W
+
+
+def test_lanes_for_length():
+    from paper_2202_02847_gb300.fmm import lanes_for_length
+    got = lanes_for_length([0, 1, 2, 3, 4, 5, 8, 9, 16, 17, 31, 32, 33, 800])
+    assert list(got) == [1, 1, 2, 4, 4, 8, 8, 16, 16, 32, 32, 32, 32, 32]
+
+
+@pytest.fixture(scope="module")
+def plan():
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_2202_02847_gb300.fmm import AdaptivePass
+    pts, q = W.plummer(20000, seed=7)
+    tree = W.adaptive_octree(pts, leaf_size=16)
+    P = W.order_by_level(tree, lo=4, span=12)
+    pairs = W.dual_tree_m2l(tree, 0.5)
+    return tree, P, pairs, AdaptivePass(tree, P, None, device="cpu", pairs=pairs)
+
+
+def test_waves_hold_every_pair_once(plan):
+    tree, P, (src, tgt), ap = plan
+    got = sorted((int(t), int(s)) for d in ap.waves
+                 for t, s in zip(d["host"]["tgt"], d["host"]["src"]))
+    assert got == sorted(zip(tgt.tolist(), src.tolist()))
+
+
+def test_classes_partition_rows_with_uniform_orders_and_lanes(plan):
+    from paper_2202_02847_gb300.fmm import lanes_for_length
+    tree, P, _, ap = plan
+    P = np.asarray(P)
+    for d in ap.waves:
+        h = d["host"]
+        offs, row_tgt = h["offs"], h["row_tgt"]
+        assert len(set(row_tgt.tolist())) == len(row_tgt)        # a target once per wave
+        lens = np.diff(offs)
+        end = 0
+        for op, pi, po, tb, te, lanes in d["classes"]:
+            assert op == "m2l" and tb == end and te > tb
+            end = te
+            for r in range(tb, te):
+                srcs = h["src"][offs[r]:offs[r + 1]]
+                assert np.all(P[srcs] == pi) and P[row_tgt[r]] == po
+            assert np.all(np.diff(lens[tb:te]) <= 0)              # longest lists first
+            assert np.all(lanes_for_length(lens[tb:te]) == lanes)
+        assert end == len(row_tgt)
+        assert len(d["classes"]) <= 256
