@@ -221,6 +221,18 @@ def oracle_parity_and_rate(fp, tree, dev_result, picks, budget_s):
     return err, done / t_used, done, used
 
 
+def octree_config(tree, depth, dtype, world):
+    """The config object of the octree-pass workload (both arms report it)."""
+    m2l = int(sum(tree.levels[l].m2l_offsets[-1] for l in range(2, depth + 1)))
+    return {"workload": f"plain {dtype.upper()} P=10: uniform octree level {depth} "
+                        f"({2 ** depth}^3 leaves), 1M uniform points, full M2M/M2L/L2L "
+                        "translation pass",
+            "P": P, "depth": depth, "points_per_rank": NPOINTS,
+            "m2l_per_step": m2l, "m2m_per_step": sum(8 ** l for l in range(1, depth + 1)),
+            "l2l_per_step": sum(8 ** l for l in range(3, depth + 1)), "l2_flush": True,
+            "parallelism": f"{world} independent octrees (one per GPU)"}
+
+
 def run_reference(args):
     """--impl reference: the oracle as it stands on the host cores, on
     bounded samples of the same M2L workload."""
@@ -259,10 +271,10 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "plain FP64 P=10 uniform octree level 5 M2L list (oracle, "
-                               "sample of 4000 translations per step)", "P": P},
+        "config": octree_config(tree, DEPTH, "f64", args.gpus),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
-                         "sample": f"{per_step} seeded translations of the level-5 M2L list per step"},
+                         "sample": f"M2L only: {per_step} seeded translations of the level-5 M2L "
+                                   "list per step, sources' multipoles by the oracle's P2M"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -663,13 +675,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
         "data": "synthetic",
-        "config": {"workload": f"plain {args.dtype.upper()} P=10: uniform octree level {depth} "
-                               f"({2 ** depth}^3 leaves), 1M uniform points, full M2M/M2L/L2L "
-                               "translation pass",
-                   "P": P, "depth": depth, "points_per_rank": NPOINTS,
-                   "m2l_per_step": m2l_per_step, "m2m_per_step": fp.counts["m2m"],
-                   "l2l_per_step": fp.counts["l2l"], "l2_flush": True,
-                   "parallelism": f"{world} independent octrees (one per GPU)"},
+        "config": octree_config(tree, depth, args.dtype, world),
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(leafM.numel() * leafM.element_size()),
