@@ -664,7 +664,7 @@ def main():
     wbytes = 8 if args.dtype == "f64" else 4
     roof = {"bound": "alu", "achieved": flop / m2l_mean_s / 1e12, "peak": peak / 1e12,
             "unit": "TFLOP/s", "frac": flop / m2l_mean_s / peak,
-            "traffic": ncu_traffic() if args.dtype == "f64" else None,
+            "traffic": ncu_traffic() if args.dtype == "f64" and depth == DEPTH else None,
             "kernel": f"ulists_kernel<{'double' if args.dtype == 'f64' else 'float'}, P=10, M2L, G=32>"
                       " (one launch per step)",
             "m2l_ms_mean": m2l_mean_s * 1e3,
