@@ -283,7 +283,7 @@ def run_reference(args):
 def run_precision(args):
     """Precision workload: level 5 of the uniform octree (32^3 boxes, 1M points,
     seed 3) at P = 16.  The level's 5,398,920 M2L run three ways on the same
-    multipoles: shift-grouped on the tensor cores (3xTF32, FP64 target sums),
+    multipoles: shift-grouped on the tensor cores (BF16 split in 3 parts, FP64 target sums),
     rotation-based in FP64, rotation-based in FP32; errors are stated against
     the FP64 rotation path (itself checked against the oracle on sampled
     targets by the test suite)."""
@@ -319,7 +319,7 @@ def run_precision(args):
     sh32 = sh64.float()
     loffs = torch.tensor(lv.m2l_offsets, device="cuda")
     runs = {
-        "tensor_3xtf32": lambda: grid.m2l(lv.h, M, L_tc),
+        "tensor_3xbf16": lambda: grid.m2l(lv.h, M, L_tc),
         "rotation_fp64": lambda: sfmm.translate_lists(h64, "m2l", src64, sh64, loffs, out64, Pp, Pp, nb),
         "rotation_fp32": lambda: sfmm.translate_lists(h32, "m2l", src32, sh32, loffs, out32, Pp, Pp, nb),
     }
@@ -343,36 +343,40 @@ def run_precision(args):
             times[name] = float(np.median(ms))
     assert h64.sync_status() == 0 and h32.sync_status() == 0
     ref = L64.cpu().numpy()
-    err = {"tensor_3xtf32": U.rel_err(L_tc.cpu().numpy(), ref, Pp, "L"),
+    err = {"tensor_3xbf16": U.rel_err(L_tc.cpu().numpy(), ref, Pp, "L"),
            "rotation_fp32": U.rel_err(L32.double().cpu().numpy(), ref, Pp, "L"),
            "rotation_fp64": 0.0}
     w = U.weights(Pp, "L")
     per_target = {k: np.linalg.norm((a - ref) * w, axis=1) / np.linalg.norm(ref * w, axis=1)
-                  for k, a in (("tensor_3xtf32", L_tc.cpu().numpy()),
+                  for k, a in (("tensor_3xbf16", L_tc.cpu().numpy()),
                                ("rotation_fp32", L32.double().cpu().numpy()))}
     err_max = {k: float(v.max()) for k, v in per_target.items()}
     ntr = int(lv.m2l_offsets[-1])
     dense_flop = 2 * (Pp * Pp) ** 2 * ntr                  # algorithmic, one dense product
-    tf32_peak = 1917.3e12 * 1.1 / 2.25                      # measured bf16 x nominal tf32/bf16
+    bf16_peak = 1917.3e12                                   # measured dense bf16 (burst)
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(peaks_path):
-        tf32_peak = float(json.load(open(peaks_path)).get("bf16_tflops", 1917.3)) * 1e12 * 1.1 / 2.25
-    t_tc = times["tensor_3xtf32"] * 1e-3
+        bf16_peak = float(json.load(open(peaks_path)).get("bf16_tflops", 1917.3)) * 1e12
+    issued = 6 * 2 * (Pp * Pp) ** 2 * 189 * nb              # six BF16 products, 189 offsets per target
+    t_tc = times["tensor_3xbf16"] * 1e-3
     line = {
         "metric": METRIC + " (precision: level-5 M2L at P=16)",
         "value": ntr / t_tc, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": times["tensor_3xtf32"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "3xtf32 (fp64 target sums)", "data": "synthetic",
+        "ms_per_step": times["tensor_3xbf16"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "3xbf16 (fp64 target sums)", "data": "synthetic",
         "config": {"workload": "precision: uniform octree level 5 (32^3 boxes), 1M points seed 3, "
                                "P=16, 5,398,920 M2L grouped by the 316 integer offsets", "P": Pp,
                    "m2l": ntr, "l2_flush": True},
         "roofline": {"bound": "tensor", "achieved": dense_flop / t_tc / 1e12,
-                     "peak": tf32_peak / 1e12, "unit": "TFLOP/s",
-                     "frac": dense_flop / t_tc / tf32_peak, "traffic": None,
-                     "kernel": "grid_gemm_kernel (tcgen05.mma kind::tf32, 3 products)",
-                     "tensor_flop_issued_per_pass": 3 * 2 * (Pp * Pp) ** 2 * 189 * nb,
-                     "issued_tflops": 3 * 2 * (Pp * Pp) ** 2 * 189 * nb / t_tc / 1e12,
-                     "peak_note": "measured bf16 burst x nominal tf32/bf16 (1.1/2.25)"},
+                     "peak": bf16_peak / 1e12, "unit": "TFLOP/s",
+                     "frac": dense_flop / t_tc / bf16_peak, "traffic": None,
+                     "kernel": "grid_gemm_kernel (tcgen05.mma kind::f16: BF16 split in 3 parts, 6 products)",
+                     "tensor_flop_issued_per_pass": issued,
+                     "issued_tflops": issued / t_tc / 1e12,
+                     "issued_frac": issued / t_tc / bf16_peak,
+                     "note": "achieved = one dense product per translation (7.1e11 FLOP per pass); "
+                             "issued = the six BF16 products of the split, halo included; peak = "
+                             "measured dense BF16 (burst); time = the whole call (pack, GEMM, unpack)"},
         "paths_ms": times,
         "paths_translations_per_s": {k: ntr / (v * 1e-3) for k, v in times.items()},
         "rel_err_vs_fp64_rotation": err,

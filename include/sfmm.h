@@ -240,10 +240,11 @@ sfmm_status sfmm_reserve_scratch(sfmm_handle h, int p_in_max);
  * also allocates the workspaces (synchronous).
  * sfmm_grid_m2l: L (+)= M2L of every box's interaction list on an nside^3 grid
  * (nside a multiple of 8, box i at (ix*nside + iy)*nside + iz, solids of order
- * 16 stored contiguously, FP64 device arrays M and L).  Products run in
- * 3xTF32 (hi*hi + hi*lo + lo*hi, about 21 bits) with FP32 accumulation over 8
- * offsets and FP64 accumulation per target; results agree with the FP64
- * rotation path to about 1e-6 (weighted coefficient error).  Asynchronous on
+ * 16 stored contiguously, FP64 device arrays M and L).  Operands are split
+ * into three BF16 parts (hi + mid + lo, about 24 bits) and multiplied as six
+ * BF16 products with FP32 accumulation over 2 offsets and FP64 accumulation
+ * per target; results agree with the FP64 rotation path to about 3e-6, every
+ * target within 1e-5 (weighted coefficient error).  Asynchronous on
  * `stream`; one call at a time per grid object.  A device-side wait that gives
  * up sets bit 4 of the handle's status word (sfmm_sync_status).
  * Errors: SFMM_ERR_ARG, SFMM_ERR_ORDER (handle not FP64 or P_max < 16),

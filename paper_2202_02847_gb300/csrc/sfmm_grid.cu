@@ -12,16 +12,17 @@
 // 189 offsets, so a tile of 128 same-octant targets (64 when the grid side is
 // not a multiple of 16) is one GEMM with K = 189 * 256 on the 5th-generation
 // tensor cores:
-//   * T_u and x are split into TF32 hi + lo parts and multiplied as
-//     hi*hi + hi*lo + lo*hi (3xTF32, about 21 significant bits) with FP32
+//   * T_u and x are split into three BF16 parts, hi + mid + lo (about 24
+//     significant bits), and multiplied as the six products hi*hi, hi*mid,
+//     mid*hi, hi*lo, lo*hi, mid*mid (tcgen05.mma kind::f16) with FP32
 //     accumulation in tensor memory (two 128-row halves x 128 columns, two
 //     buffers);
 //   * every 2 offsets the accumulator is read out (tcgen05.ld) and added into
 //     the target's FP64 sum in global memory (FP32 rounding over longer runs
 //     of offsets pushed single targets above a 1e-5 relative error);
-//   * operand chunks (16 of K) are staged in shared memory in four stages: the
+//   * operand chunks (16 of K) are staged in shared memory in five stages: the
 //     T_u chunk, stored pre-tiled, by one bulk copy; the targets' source
-//     vectors, stored split by coordinate parity, by two 5-D tensor copies;
+//     vectors, stored split by coordinate parity, by three 5-D tensor copies;
 //   * one thread issues copies, one issues MMAs, four warps drain the
 //     accumulators; one persistent CTA per SM.
 // T_u are built once per grid object with the FP64 rotation-based M2L on the
@@ -29,6 +30,7 @@
 // time-out the kernel records SFMM_GRID_TIMEOUT in the status word, stops
 // issuing work, frees its tensor memory and returns.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -47,10 +49,11 @@ namespace {
 
 constexpr int GP = 16;             // order of the grid operators
 constexpr int KD = GP * GP;        // 256 reals per box in the reduced layout
-constexpr int KC = 16;             // K chunk staged in shared memory
-constexpr int NST = 4;             // pipeline stages
+constexpr int KC = 16;             // K chunk staged in shared memory (one BF16 MMA)
+constexpr int NST = 5;             // pipeline stages
 constexpr int NKC = KD / KC;       // chunks per offset
-constexpr int A_PART = KD * KC * 4;   // one operand part (hi or lo) of an A chunk: 16 KB
+constexpr int NPART = 3;           // operand parts: hi, mid, lo (BF16 each)
+constexpr int A_PART = KD * KC * 2;   // one part of an A chunk: 256 rows x 16 K x 2 B = 8 KB
 constexpr int FLUSH = 2;           // offsets accumulated in FP32 before an FP64 flush
 constexpr int NU = 189;            // offsets of a child octant
 constexpr int NCH_ALL = NU * NKC;  // K chunks of a tile
@@ -85,15 +88,40 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
     return d;
 }
 
-// byte offset of (row r, k) inside a [rows x KC] K-major tile
+// byte offset of (row r, k) inside a [rows x KC] BF16 K-major tile of core
+// matrices of 8 rows x 8 K (16 bytes per row)
 __device__ __forceinline__ int koff(int r, int k) {
-    return ((r >> 3) * (KC / 4) + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4;
+    return ((r >> 3) * (KC / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-__device__ __forceinline__ float tf32_round(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+// v = hi + mid + lo in BF16 (8 significant bits each): the three parts carry
+// about 24 bits of v, the products dropped below (mid*lo, lo*mid, lo*lo) are
+// of relative size 2^-24
+__device__ __forceinline__ void split3(double v, unsigned short *hi, unsigned short *mid,
+                                       unsigned short *lo) {
+    // (FP64 arithmetic: used once per operator entry when a grid is created)
+    const __nv_bfloat16 h = __double2bfloat16(v);
+    const double r1 = v - (double)__bfloat162float(h);
+    const __nv_bfloat16 m = __double2bfloat16(r1);
+    const double r2 = r1 - (double)__bfloat162float(m);
+    const __nv_bfloat16 l = __double2bfloat16(r2);
+    *hi = __bfloat16_as_ushort(h);
+    *mid = __bfloat16_as_ushort(m);
+    *lo = __bfloat16_as_ushort(l);
+}
+
+// the same split of an FP32 value in FP32 arithmetic (the subtractions are
+// exact): the per-call packing of the sources, where FP64 work would cost more
+// than the copy itself on this GPU's FP64 pipe
+__device__ __forceinline__ void split3f(float v, unsigned short *hi, unsigned short *mid,
+                                        unsigned short *lo) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(m);
+    *hi = __bfloat16_as_ushort(h);
+    *mid = __bfloat16_as_ushort(m);
+    *lo = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
 }
 
 // ----------------------------------------------------------------- kernels
@@ -103,11 +131,12 @@ struct Scales {
     double s[GP * (GP + 1) / 2];
 };
 
-// x = M c / h^{k+1} in the reduced layout on the halo grid, split into TF32 hi, lo.
+// x = M c / h^{k+1} in the reduced layout on the halo grid, split into BF16 hi, mid, lo.
 // The halo grid (side nh = nside + 6, even) is stored split by coordinate
 // parity, [px py pz][hx/2][hy/2][hz/2][KD], so that the sources of a tile of
 // same-parity targets under one offset form one dense box.
-__global__ void pack_kernel(const double *M, int nside, Scales sc, float *xhi, float *xlo) {
+__global__ void pack_kernel(const double *M, int nside, Scales sc, unsigned short *xhi,
+                            unsigned short *xmid, unsigned short *xlo) {
     const int nh = nside + 6, nh2 = nh / 2;
     const long long total = (long long)nh * nh * nh * KD;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -128,9 +157,7 @@ __global__ void pack_kernel(const double *M, int nside, Scales sc, float *xhi, f
             const double val = s[n * (n + 1) + (im ? n + 1 + m : m)];
             v = (float)(val * sc.s[n * (n + 1) / 2 + m]);
         }
-        const float hi = tf32_round(v);
-        xhi[i] = hi;
-        xlo[i] = v - hi;
+        split3f(v, xhi + i, xmid + i, xlo + i);
     }
 }
 
@@ -156,9 +183,9 @@ __global__ void unpack_kernel(const double *y, int nside, Scales sc, double *L, 
 }
 
 // operators: T[code][e'][j] from the FP64 M2L of basis vector j (raw solid of
-// order GP), converted to y = L / c in the reduced layout and split hi/lo.
+// order GP), converted to y = L / c in the reduced layout and split hi/mid/lo.
 __global__ void operator_kernel(const double *L, const int *codes, int ncodes, const double *c,
-                                float *thi) {
+                                unsigned short *top) {
     const long long total = (long long)ncodes * KD * KD;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -169,19 +196,18 @@ __global__ void operator_kernel(const double *L, const int *codes, int ncodes, c
         bool im;
         reduced_index(ep, &n, &m, &im);
         const double *s = L + ((long long)k * KD + j) * (GP * (GP + 1));
-        const float v = (float)(s[n * (n + 1) + (im ? n + 1 + m : m)] / c[n * (n + 1) / 2 + m]);
-        const float hi = tf32_round(v);
-        // pre-tiled: [code][chunk][hi|lo][K-major core-matrix tile of 256 rows x KC]
+        const double v = s[n * (n + 1) + (im ? n + 1 + m : m)] / c[n * (n + 1) / 2 + m];
+        // pre-tiled: [code][chunk][hi|mid|lo][K-major core-matrix tile of 256 rows x KC]
         const int ch = j / KC, kk = j % KC;
-        unsigned char *base = reinterpret_cast<unsigned char *>(thi) +
-                              ((long long)codes[k] * NKC + ch) * 2 * A_PART;
-        *reinterpret_cast<float *>(base + koff(ep, kk)) = hi;
-        *reinterpret_cast<float *>(base + A_PART + koff(ep, kk)) = v - hi;
+        unsigned char *base = reinterpret_cast<unsigned char *>(top) +
+                              ((long long)codes[k] * NKC + ch) * NPART * A_PART + koff(ep, kk);
+        split3(v, reinterpret_cast<unsigned short *>(base), reinterpret_cast<unsigned short *>(base + A_PART),
+               reinterpret_cast<unsigned short *>(base + 2 * A_PART));
     }
 }
 
 struct GemmArgs {
-    const float *thi;           // pre-tiled operators, [NCODE][NKC][hi|lo][A_PART bytes]
+    const unsigned short *top;  // pre-tiled operators, [NCODE][NKC][hi|mid|lo][A_PART bytes]
     double *y;                  // [ns^3][KD], FP64 sums, zeroed before the launch
     int nside;
     int *status;
@@ -220,17 +246,18 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, vol
 constexpr int GW = NKC * FLUSH;
 constexpr int NSLAB = (NCH_ALL + GW - 1) / GW;
 
-// dynamic shared memory: NST stages of A (hi, lo) and B (hi, lo), then 8 KB for
-// the mbarriers, the TMEM slot, the abort flag and the offset codes of the 8 octants
+// dynamic shared memory: NST stages of A (hi, mid, lo) and B (hi, mid, lo), then
+// 8 KB for the mbarriers, the TMEM slot, the abort flag and the offset codes of
+// the 8 octants
 template <int NT>
-constexpr int smem_gemm() { return NST * (2 * A_PART + 2 * NT * KC * 4) + 8192; }
+constexpr int smem_gemm() { return NST * (NPART * A_PART + NPART * NT * KC * 2) + 8192; }
 
 // Persistent, warp-specialised GEMM over (K slab, tile) units dealt round-robin.
 //   warp 4, one thread: copies.  For chunk i it waits until the MMAs of chunk
 //     i - NST have freed the stage (`empty`), sets the stage's `full` mbarrier
 //     to expect the chunk's bytes and issues one bulk copy of the pre-tiled
-//     T_u chunk (A, hi and lo) and two 5-D tensor copies of the targets'
-//     source vectors (B, hi and lo, 64-byte swizzled rows).
+//     T_u chunk (A, hi, mid and lo) and three 5-D tensor copies of the
+//     targets' source vectors (B, hi, mid and lo, 32-byte swizzled rows).
 //   warp 5, one thread: MMA issue.  For chunk i it waits on `full`, issues the
 //     chunk's tcgen05.mma into one of two accumulator buffers and commits them
 //     to the stage's `empty` mbarrier; the last chunk of a unit is also
@@ -245,10 +272,11 @@ constexpr int smem_gemm() { return NST * (2 * A_PART + 2 * NT * KC * 4) + 8192; 
 // for their work in flight, and the CTA frees its tensor memory and returns.
 template <int NT>
 __global__ void __launch_bounds__(192, 1)
-grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo) {
+grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_mid,
+                 const __grid_constant__ CUtensorMap tm_lo) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    constexpr int B_PART = NT * KC * 4;             // 8 or 4 KB
-    constexpr int STAGE = 2 * A_PART + 2 * B_PART;
+    constexpr int B_PART = NT * KC * 2;             // 4 or 2 KB
+    constexpr int STAGE = NPART * A_PART + NPART * B_PART;
     constexpr int TZ = NT / 16;                     // tile depth along z
     constexpr uint32_t TCOLS = 4 * NT;              // 2 buffers x 2 row halves x NT columns
     uint64_t *full = reinterpret_cast<uint64_t *>(sm + NST * STAGE);
@@ -325,7 +353,7 @@ grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __
                         c2 = ty * 4 + (sy >> 1);
                         c3 = tx * 4 + (sx >> 1);
                         c4 = ((sx & 1) << 2) | ((sy & 1) << 1) | (sz & 1);
-                        abase = reinterpret_cast<const unsigned char *>(a.thi) + (long long)code * NKC * 2 * A_PART;
+                        abase = reinterpret_cast<const unsigned char *>(a.top) + (long long)code * NKC * NPART * A_PART;
                     }
                     const int stg = (int)(i % NST), kc = (ci % NKC) * KC;
                     if (i >= NST && !wait_or_abort(smem_u32(empty + stg), (uint32_t)(((i / NST) - 1) & 1), abort_flag)) {
@@ -334,18 +362,17 @@ grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __
                         break;
                     }
                     const uint32_t dst = smem_u32(sm + stg * STAGE), bar = smem_u32(full + stg);
-                    const unsigned char *src = abase + (long long)(ci % NKC) * 2 * A_PART;
+                    const unsigned char *src = abase + (long long)(ci % NKC) * NPART * A_PART;
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(STAGE) : "memory");
                     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                                 :: "r"(dst), "l"(src), "r"(2 * A_PART), "r"(bar) : "memory");
-                    asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                                 " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
-                                 :: "r"(dst + 2 * A_PART), "l"(reinterpret_cast<uint64_t>(&tm_hi)),
-                                    "r"(kc), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar) : "memory");
-                    asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                                 " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
-                                 :: "r"(dst + 2 * A_PART + B_PART), "l"(reinterpret_cast<uint64_t>(&tm_lo)),
-                                    "r"(kc), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar) : "memory");
+                                 :: "r"(dst), "l"(src), "r"(NPART * A_PART), "r"(bar) : "memory");
+                    const CUtensorMap *maps[NPART] = {&tm_hi, &tm_mid, &tm_lo};
+#pragma unroll
+                    for (int p = 0; p < NPART; ++p)
+                        asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                                     " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+                                     :: "r"(dst + NPART * A_PART + p * B_PART), "l"(reinterpret_cast<uint64_t>(maps[p])),
+                                        "r"(kc), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar) : "memory");
                     last[stg] = i;
                 }
             }
@@ -356,12 +383,15 @@ grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __
         __syncwarp();
     } else if (warp == 5) {
         if (lane == 0) {
-            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) |
+            // D = FP32, A = B = BF16, both K-major, N = NT, M = 128
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
                                    ((uint32_t)(128 >> 4) << 24);
-            // descriptors of stage 0; stage s adds s * STAGE to the address field
+            // descriptors of stage 0; stage s adds s * STAGE to the address field.
+            // A: no swizzle, core matrices 128 B apart along K, 8-row groups (KC / 8) * 128 B
+            // apart; B: 32-byte swizzle, 8-row groups of 32-byte rows 256 B apart
             const uint32_t s0 = smem_u32(sm);
-            const uint64_t dA = sdesc(s0, 128, (KC / 4) * 128, 0);
-            const uint64_t dB = sdesc(s0 + 2 * A_PART, 16, 512, 4);
+            const uint64_t dA = sdesc(s0, 128, (KC / 8) * 128, 0);
+            const uint64_t dB = sdesc(s0 + NPART * A_PART, 16, 256, 6);
             long long i = 0, g = 0, last_mma = -1;
             bool ok = true;
             for (int u = blockIdx.x; u < n_units && ok; u += G, ++g) {
@@ -383,23 +413,20 @@ grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     const uint64_t so = (uint64_t)((stg * STAGE) >> 4);
+                    // six products of the parts, (hi, hi) first; the rows of half h
+                    // start (128 / 8) * (KC / 8) * 128 bytes into each A part
+                    constexpr int PA[6] = {0, 0, 1, 0, 2, 1}, PB[6] = {0, 1, 0, 2, 0, 1};
 #pragma unroll
                     for (int h = 0; h < 2; ++h)
 #pragma unroll
-                        for (int s = 0; s < KC / 8; ++s) {
-                            const uint64_t ahi = dA + so + ((h * (A_PART / 2) + s * 256) >> 4);
-                            const uint64_t alo = ahi + (A_PART >> 4);
-                            const uint64_t bhi = dB + so + ((s * 32) >> 4);
-                            const uint64_t blo = bhi + (B_PART >> 4);
+                        for (int t = 0; t < 6; ++t) {
+                            const uint64_t ad = dA + so + ((PA[t] * A_PART + h * (A_PART / 2)) >> 4);
+                            const uint64_t bd = dB + so + ((PB[t] * B_PART) >> 4);
                             const uint32_t d = dcol + h * NT;
-                            const uint32_t acc0 = (ci == c_begin && s == 0) ? 0u : 1u;
+                            const uint32_t acc = (ci == c_begin && t == 0) ? 0u : 1u;
                             asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-                                         :: "r"(d), "l"(ahi), "l"(bhi), "r"(idesc), "r"(acc0));
-                            asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
-                                         :: "r"(d), "l"(ahi), "l"(blo), "r"(idesc));
-                            asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
-                                         :: "r"(d), "l"(alo), "l"(bhi), "r"(idesc));
+                                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                                         :: "r"(d), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
                         }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                                  :: "r"(smem_u32(empty + stg)) : "memory");
@@ -472,12 +499,12 @@ grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __
 struct sfmm_grid_ctx {
     sfmm_handle h = nullptr;
     int P = GP, nside = 0;
-    float *thi = nullptr;                    // operators, pre-tiled hi|lo chunks
-    float *xhi = nullptr, *xlo = nullptr;    // packed sources on the halo grid
+    unsigned short *top = nullptr;           // operators, pre-tiled hi|mid|lo BF16 chunks
+    unsigned short *xhi = nullptr, *xmid = nullptr, *xlo = nullptr;   // packed sources (BF16 parts)
     double *y = nullptr;                     // FP64 accumulators
     double *c = nullptr;                     // sqrt((n-m)!(n+m)!) on the device
     std::vector<double> ch;                  // and on the host
-    CUtensorMap tm_hi, tm_lo;                // 5-D maps of xhi, xlo (tile boxes of source vectors)
+    CUtensorMap tm_hi, tm_mid, tm_lo;        // 5-D maps of the source parts (tile boxes)
     int nt = 0;                              // targets per tile: 128 or 64
 };
 
@@ -488,16 +515,16 @@ using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 // map of the parity-split halo grid [8][nh/2][nh/2][nh/2][KD] (innermost last)
-// with boxes of KC reals x tz x 4 x 4 boxes x 1 parity class, 64-byte swizzle
-bool encode_source_map(EncodeTiled enc, CUtensorMap *m, float *base, int nside, int tz) {
+// with boxes of KC BF16 values x tz x 4 x 4 boxes x 1 parity class, 32-byte swizzle
+bool encode_source_map(EncodeTiled enc, CUtensorMap *m, unsigned short *base, int nside, int tz) {
     const cuuint64_t nh2 = (cuuint64_t)(nside + 6) / 2;
     const cuuint64_t dims[5] = {(cuuint64_t)KD, nh2, nh2, nh2, 8};
-    const cuuint64_t row = (cuuint64_t)KD * sizeof(float);
+    const cuuint64_t row = (cuuint64_t)KD * sizeof(unsigned short);
     const cuuint64_t strides[4] = {row, row * nh2, row * nh2 * nh2, row * nh2 * nh2 * nh2};
     const cuuint32_t box[5] = {(cuuint32_t)KC, (cuuint32_t)tz, 4, 4, 1};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, base, dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -516,14 +543,16 @@ sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out) {
     g->h = h;
     g->nside = nside;
     const long long nh = nside + 6;
-    const size_t op_bytes = (size_t)NCODE * NKC * 2 * A_PART;
-    bool ok = cudaMalloc(&g->thi, op_bytes) == cudaSuccess &&
-              cudaMalloc(&g->xhi, sizeof(float) * (size_t)(nh * nh * nh) * KD) == cudaSuccess &&
-              cudaMalloc(&g->xlo, sizeof(float) * (size_t)(nh * nh * nh) * KD) == cudaSuccess &&
+    const size_t op_bytes = (size_t)NCODE * NKC * NPART * A_PART;
+    const size_t x_bytes = sizeof(unsigned short) * (size_t)(nh * nh * nh) * KD;
+    bool ok = cudaMalloc(&g->top, op_bytes) == cudaSuccess &&
+              cudaMalloc(&g->xhi, x_bytes) == cudaSuccess &&
+              cudaMalloc(&g->xmid, x_bytes) == cudaSuccess &&
+              cudaMalloc(&g->xlo, x_bytes) == cudaSuccess &&
               cudaMalloc(&g->y, sizeof(double) * (size_t)nside * nside * nside * KD) == cudaSuccess &&
               cudaMalloc(&g->c, sizeof(double) * GP * (GP + 1) / 2) == cudaSuccess;
     if (!ok) { sfmm_grid_destroy(g); return SFMM_ERR_NOMEM; }
-    cudaMemset(g->thi, 0, op_bytes);
+    cudaMemset(g->top, 0, op_bytes);
     std::vector<double> c(GP * (GP + 1) / 2);
     {
         std::vector<double> f(2 * GP + 1, 1.0);
@@ -586,7 +615,7 @@ sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out) {
                             reinterpret_cast<void *const *>(dpout), dshift, GP, GP, count, 0, nullptr);
     }
     if (st == SFMM_OK) {
-        operator_kernel<<<1024, 256>>>(dL, dcodes, ncodes, g->c, g->thi);
+        operator_kernel<<<1024, 256>>>(dL, dcodes, ncodes, g->c, g->top);
         if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) st = SFMM_ERR_CUDA;
     }
     cudaFree(dbasis);
@@ -606,6 +635,7 @@ sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out) {
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
             q != cudaDriverEntryPointSuccess || fn == nullptr ||
             !encode_source_map(reinterpret_cast<EncodeTiled>(fn), &g->tm_hi, g->xhi, nside, g->nt / 16) ||
+            !encode_source_map(reinterpret_cast<EncodeTiled>(fn), &g->tm_mid, g->xmid, nside, g->nt / 16) ||
             !encode_source_map(reinterpret_cast<EncodeTiled>(fn), &g->tm_lo, g->xlo, nside, g->nt / 16))
             st = SFMM_ERR_CUDA;
     }
@@ -620,8 +650,9 @@ sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out) {
 sfmm_status sfmm_grid_destroy(sfmm_grid g) {
     if (g == nullptr) return SFMM_OK;
     cudaDeviceSynchronize();
-    cudaFree(g->thi);
+    cudaFree(g->top);
     cudaFree(g->xhi);
+    cudaFree(g->xmid);
     cudaFree(g->xlo);
     cudaFree(g->y);
     cudaFree(g->c);
@@ -644,15 +675,15 @@ sfmm_status sfmm_grid_m2l(sfmm_grid g, double box_size, const void *M, void *L, 
             su.s[n * (n + 1) / 2 + m] = g->ch[n * (n + 1) / 2 + m] / hn;
         }
     }
-    pack_kernel<<<2048, 256, 0, s>>>(reinterpret_cast<const double *>(M), ns, sp, g->xhi, g->xlo);
+    pack_kernel<<<2048, 256, 0, s>>>(reinterpret_cast<const double *>(M), ns, sp, g->xhi, g->xmid, g->xlo);
     // tiles of 4 x 4 x (nt / 16) same-octant targets; one persistent CTA per SM
     // deals the (K slab, tile) units round-robin
-    GemmArgs a{g->thi, g->y, ns, g->h->d_status};
+    GemmArgs a{g->top, g->y, ns, g->h->d_status};
     const int ctas = g->h->sm_count > 0 ? g->h->sm_count : 1;
     if (g->nt == 128)
-        grid_gemm_kernel<128><<<ctas, 192, smem_gemm<128>(), s>>>(a, g->tm_hi, g->tm_lo);
+        grid_gemm_kernel<128><<<ctas, 192, smem_gemm<128>(), s>>>(a, g->tm_hi, g->tm_mid, g->tm_lo);
     else
-        grid_gemm_kernel<64><<<ctas, 192, smem_gemm<64>(), s>>>(a, g->tm_hi, g->tm_lo);
+        grid_gemm_kernel<64><<<ctas, 192, smem_gemm<64>(), s>>>(a, g->tm_hi, g->tm_mid, g->tm_lo);
     unpack_kernel<<<2048, 256, 0, s>>>(g->y, ns, su, reinterpret_cast<double *>(L), accumulate);
     return cudaGetLastError() == cudaSuccess ? SFMM_OK : SFMM_ERR_CUDA;
 }

@@ -9,7 +9,7 @@ the M2M-combined multipoles of its children at the same order).
   level-3 targets.  A second run of the same launches gives bitwise the same
   locals (the lists kernels add in a fixed order).
 * The same tree at P = 16 through the tensor-core grid M2L of level 5
-  (3xTF32 products, FP64 target sums): 3 sampled targets at the FP32-class
+  (three-part BF16 split, FP64 target sums): 3 sampled targets at the FP32-class
   tolerance."""
 import numpy as np
 import pytest

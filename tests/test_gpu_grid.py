@@ -9,7 +9,7 @@ import gpu_util as U
 pytestmark = pytest.mark.gpu
 
 P = 16
-TOL = 1e-5     # FP32-class: 3xTF32 products, FP64 target sums
+TOL = 1e-5     # FP32-class: three-part BF16 split, FP64 target sums
 
 
 @pytest.fixture(scope="module")
