@@ -369,6 +369,7 @@ sfmm_status sfmm_create(int P_max, sfmm_dtype dtype, sfmm_handle *out) {
     }
     sfmm_status st = dtype == SFMM_F64 ? upload<double>(ht, h, &h->t64) : upload<float>(ht, h, &h->t32);
     if (st == SFMM_OK && cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess) st = SFMM_ERR_NOMEM;
+    if (st == SFMM_OK && cudaMalloc(&h->d_work, sizeof(unsigned long long)) != cudaSuccess) st = SFMM_ERR_NOMEM;
     if (st == SFMM_OK && cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) st = SFMM_ERR_CUDA;
     if (st == SFMM_OK) {
         const size_t esz = dtype == SFMM_F64 ? sizeof(double) : sizeof(float);
@@ -394,6 +395,8 @@ sfmm_status sfmm_create(int P_max, sfmm_dtype dtype, sfmm_handle *out) {
     if (st != SFMM_OK) {
         cudaFree(h->d_tables);
         cudaFree(h->d_status);
+    cudaFree(h->d_work);
+        cudaFree(h->d_work);
         cudaFree(h->d_scratch);
         if (h->scratch_free) cudaEventDestroy(h->scratch_free);
         delete h;
@@ -408,6 +411,7 @@ sfmm_status sfmm_destroy(sfmm_handle h) {
     cudaDeviceSynchronize();
     cudaFree(h->d_tables);
     cudaFree(h->d_status);
+    cudaFree(h->d_work);
     cudaFree(h->d_scratch);
     if (h->scratch_free) cudaEventDestroy(h->scratch_free);
     delete h;
@@ -588,6 +592,8 @@ static sfmm_status launch_multi(sfmm_handle h, const sfmm_list_class *classes, i
     g.smem = (size_t)w * per_warp;
     g.blocks = blocks;
     ScratchGuard guard(h, stream, true);
+    mp.work = h->d_work;                          // chunks are handed out by this counter
+    if (cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), stream) != cudaSuccess) return SFMM_ERR_CUDA;
     multi_launch<T>(h, g, stream, tb, mp, reinterpret_cast<const T *const *>(src), reinterpret_cast<const T *>(shift),
                     offsets, reinterpret_cast<T *const *>(out), accumulate, reinterpret_cast<T *>(h->d_scratch),
                     h->d_status);

@@ -516,6 +516,7 @@ struct MultiClass {
     long long tb, te, chunk_begin;
 };
 struct MultiParams {
+    unsigned long long *work;    // zeroed before the launch; warps take chunks from it
     int n;
     int x_slot;                  // scratch elements per lane
     int row_slot;                // shared elements per lane
@@ -534,10 +535,13 @@ __global__ void __launch_bounds__(256, 1) multi_lists_kernel(DevTables<T> tb, Mu
     const long long slot = (long long)blockIdx.x * (blockDim.x / WARP) + warp;
     LaneArr<T> X{scratch + slot * mp.x_slot * WARP + lane};
     LaneArr<T> buf{reinterpret_cast<T *>(smem_raw) + (size_t)warp * mp.row_slot * WARP + lane};
-    const long long nw = (long long)gridDim.x * (blockDim.x / WARP);
-    for (long long r = 0; r * nw < mp.total_chunks; ++r) {
-        const long long c = deal_chunk(r, nw, slot);
-        if (c >= mp.total_chunks) continue;
+    for (;;) {
+        // dynamic deal: classes come ordered by decreasing chunk cost, so the
+        // longest chunks start first and the short ones fill the tail
+        long long c = 0;
+        if (lane == 0) c = (long long)atomicAdd(mp.work, 1ull);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= mp.total_chunks) break;
         int k = 0, hi = mp.n - 1;                     // last class with chunk_begin <= c
         while (k < hi) {
             const int mid = (k + hi + 1) >> 1;

@@ -142,6 +142,14 @@ class UniformPass:
         return len(self.m2m) + 1 + len(self.l2l)
 
 
+def translation_cost(p_in, p_out):
+    """Relative cost of one rotation-based translation from order p_in to
+    p_out (the swaps of the input and output rows and the z-translation
+    coupling them; constant factors dropped)."""
+    z = sum((p_out - m) * (p_in - m) for m in range(min(p_in, p_out)))
+    return p_in * (p_in + 1) * (2 * p_in + 1) // 6 + p_out * (p_out + 1) * (2 * p_out + 1) // 6 + z
+
+
 def lanes_for_length(lengths):
     """Lanes per target for lists of the given lengths: the smallest power of
     two >= the length, capped at 32 (one warp); 1 for lists of 0 or 1 source.
@@ -242,6 +250,11 @@ class AdaptivePass:
                         or row_lanes[r] != row_lanes[cs]):
                     classes.append(("m2l", int(row_pi[cs]), int(row_po[cs]), cs, r, int(row_lanes[cs])))
                     cs = r
+            # the fused launch hands out chunks in class order: most expensive
+            # first chunk first (its longest list, ceil(length / lanes) rounds
+            # of translations of that order pair)
+            row_len = np.diff(offs)
+            classes.sort(key=lambda c: -(-(-row_len[c[3]] // c[5]) * translation_cost(c[1], c[2])))
             self.waves.append(dict(
                 classes=classes, n=len(rows),
                 src=self.ptrM(ws), out=self.ptrL(row_tgt),

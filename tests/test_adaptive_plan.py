@@ -31,7 +31,7 @@ def test_waves_hold_every_pair_once(plan):
 
 
 def test_classes_partition_rows_with_uniform_orders_and_lanes(plan):
-    from paper_2202_02847_gb300.fmm import lanes_for_length
+    from paper_2202_02847_gb300.fmm import lanes_for_length, translation_cost
     tree, P, _, ap = plan
     P = np.asarray(P)
     for d in ap.waves:
@@ -39,14 +39,17 @@ def test_classes_partition_rows_with_uniform_orders_and_lanes(plan):
         offs, row_tgt = h["offs"], h["row_tgt"]
         assert len(set(row_tgt.tolist())) == len(row_tgt)        # a target once per wave
         lens = np.diff(offs)
-        end = 0
+        covered = np.zeros(len(row_tgt), int)
+        cost = []
         for op, pi, po, tb, te, lanes in d["classes"]:
-            assert op == "m2l" and tb == end and te > tb
-            end = te
+            assert op == "m2l" and te > tb
+            covered[tb:te] += 1
+            cost.append(-(-lens[tb] // lanes) * translation_cost(pi, po))
             for r in range(tb, te):
                 srcs = h["src"][offs[r]:offs[r + 1]]
                 assert np.all(P[srcs] == pi) and P[row_tgt[r]] == po
             assert np.all(np.diff(lens[tb:te]) <= 0)              # longest lists first
             assert np.all(lanes_for_length(lens[tb:te]) == lanes)
-        assert end == len(row_tgt)
+        assert np.all(covered == 1)                               # classes partition the rows
+        assert cost == sorted(cost, reverse=True)                 # costliest first chunk first
         assert len(d["classes"]) <= 256
