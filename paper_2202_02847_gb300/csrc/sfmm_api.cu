@@ -262,9 +262,11 @@ sfmm_status launch_lists(sfmm_handle h, int op, const void *const *src, const vo
             auto S = reinterpret_cast<const T *>(shift);
             T *scr = reinterpret_cast<T *>(h->d_scratch);
             ScratchGuard guard(h, stream, true);
-            if (op == OP_M2M) glists_launch<T, OP_M2M>(h, gg, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, G, scr, h->d_status);
-            else if (op == OP_M2L) glists_launch<T, OP_M2L>(h, gg, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, G, scr, h->d_status);
-            else glists_launch<T, OP_L2L>(h, gg, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, G, scr, h->d_status);
+            if (cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), stream) != cudaSuccess) return SFMM_ERR_CUDA;
+            unsigned long long *wk = h->d_work;
+            if (op == OP_M2M) glists_launch<T, OP_M2M>(h, gg, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, G, scr, wk, h->d_status);
+            else if (op == OP_M2L) glists_launch<T, OP_M2L>(h, gg, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, G, scr, wk, h->d_status);
+            else glists_launch<T, OP_L2L>(h, gg, stream, tb, Sp, S, offsets, O, p_in, p_out, n_targets, accumulate, G, scr, wk, h->d_status);
             return cudaGetLastError() == cudaSuccess ? SFMM_OK : SFMM_ERR_CUDA;
         }
     }
@@ -395,7 +397,6 @@ sfmm_status sfmm_create(int P_max, sfmm_dtype dtype, sfmm_handle *out) {
     if (st != SFMM_OK) {
         cudaFree(h->d_tables);
         cudaFree(h->d_status);
-    cudaFree(h->d_work);
         cudaFree(h->d_work);
         cudaFree(h->d_scratch);
         if (h->scratch_free) cudaEventDestroy(h->scratch_free);

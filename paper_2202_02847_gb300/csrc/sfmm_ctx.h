@@ -17,7 +17,7 @@ struct sfmm_ctx {
     size_t smem_optin = 0;      // max dynamic shared memory per block
     void *d_tables = nullptr;   // one allocation holding every table
     int *d_status = nullptr;    // device status word (atomicOr by kernels)
-    unsigned long long *d_work = nullptr;   // work counter of the multi-class launch
+    unsigned long long *d_work = nullptr;   // chunk counter of the group-lists launches (with the scratch)
     sfmm::DevTables<double> t64{};
     sfmm::DevTables<float> t32{};
     // global scratch for orders whose rotated solid does not fit in shared

@@ -36,7 +36,8 @@ void lists_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, con
 template <typename T, int OP>
 void glists_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
                    const T *const *Sp, const T *S, const long long *offsets, T *const *O,
-                   int p_in, int p_out, long long nt, int acc, int G, T *scratch, int *status);
+                   int p_in, int p_out, long long nt, int acc, int G, T *scratch,
+                   unsigned long long *work, int *status);
 
 template <typename T>
 void multi_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,

@@ -57,9 +57,10 @@ void lists_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, con
 template <typename T, int OP>
 void glists_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
                    const T *const *Sp, const T *S, const long long *offsets, T *const *O,
-                   int p_in, int p_out, long long nt, int acc, int G, T *scratch, int *status) {
+                   int p_in, int p_out, long long nt, int acc, int G, T *scratch,
+                   unsigned long long *work, int *status) {
     auto k = glists_kernel<T, OP>;
-    k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, Sp, S, offsets, O, p_in, p_out, nt, acc, G, scratch, status);
+    k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, Sp, S, offsets, O, p_in, p_out, nt, acc, G, scratch, work, status);
 }
 
 template <typename T>
@@ -95,7 +96,7 @@ template void lists_launch<GT, GOP>(const sfmm_ctx *, const Geometry &, cudaStre
                                     long long, int, GT *, int *);
 template void glists_launch<GT, GOP>(const sfmm_ctx *, const Geometry &, cudaStream_t, const DevTables<GT> &,
                                      const GT *const *, const GT *, const long long *, GT *const *, int, int,
-                                     long long, int, int, GT *, int *);
+                                     long long, int, int, GT *, unsigned long long *, int *);
 template void set_generic_attrs<GT, GOP>(size_t);
 #else
 using GT = SFMM_GENERIC_T;

@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(256, 1) glists_kernel(DevTables<T> tb, const T
                                                      const T *shift, const long long *offsets,
                                                      T *const *out, int p_in, int p_out,
                                                      long long n_targets, int accumulate, int G,
-                                                     T *scratch, int *status) {
+                                                     T *scratch, unsigned long long *work, int *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & (WARP - 1), warp = threadIdx.x / WARP;
     const long long slot = (long long)blockIdx.x * (blockDim.x / WARP) + warp;
@@ -494,10 +494,13 @@ __global__ void __launch_bounds__(256, 1) glists_kernel(DevTables<T> tb, const T
     LaneArr<T> Y = X + ex;
     LaneArr<T> buf{reinterpret_cast<T *>(smem_raw) + (size_t)warp * row_elems(p_in, p_out) * WARP + lane};
     const int ng = WARP / G;
-    const long long nw = (long long)gridDim.x * (blockDim.x / WARP);
-    for (long long k = 0; k * nw * ng < n_targets; ++k) {
-        const long long c = deal_chunk(k, nw, slot);
-        if (c * ng >= n_targets) continue;
+    for (;;) {
+        // chunks from a counter (zeroed before the launch), in the callers'
+        // order of decreasing list length
+        long long c = 0;
+        if (lane == 0) c = (long long)atomicAdd(work, 1ull);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c * ng >= n_targets) break;
         group_chunk<T, OP>(tb, p_in, p_out, G, c * ng + lane / G, n_targets, src, shift, offsets, out,
                            accumulate, X, Y, buf, status);
     }
