@@ -41,19 +41,26 @@ void set_attrs_t(size_t smem) {
 void set_attrs(size_t smem) { set_attrs_t<Real>(smem); }
 
 // warps per block and blocks for `chunks` warp-chunks of work
+// (the block size that leaves the most warps resident per SM: with FP32
+// solids two blocks of 7 warps fit where one block of 8 would)
 template <typename T, typename K>
 bool geometry(K kernel, const Launch &L, long long chunks, int *warps, size_t *smem, long long *blocks) {
     const size_t per_warp = (size_t)S * XSTRIDE * sizeof(T);
-    int w = (int)(L.smem_optin / per_warp);
-    if (w < 1) return false;
-    if (w > 8) w = 8;
-    *warps = w;
-    *smem = (size_t)w * per_warp;
-    long long b = (chunks + w - 1) / w;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, w * 32, *smem) != cudaSuccess || nb < 1)
-        nb = 1;
-    const long long cap = (long long)nb * L.sm_count;
+    int wmax = (int)(L.smem_optin / per_warp);
+    if (wmax < 1) return false;
+    if (wmax > 8) wmax = 8;
+    int best_w = 0, best_nb = 0;
+    for (int w = wmax; w >= 1; --w) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, w * 32, (size_t)w * per_warp) != cudaSuccess)
+            nb = 0;
+        if (nb > 0 && w * nb > best_w * best_nb) { best_w = w; best_nb = nb; }
+    }
+    if (best_w < 1) { best_w = wmax; best_nb = 1; }
+    *warps = best_w;
+    *smem = (size_t)best_w * per_warp;
+    const long long b = (chunks + best_w - 1) / best_w;
+    const long long cap = (long long)best_nb * L.sm_count;
     *blocks = b < cap ? b : cap;
     return *blocks >= 1;
 }
