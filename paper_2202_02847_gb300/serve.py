@@ -16,8 +16,11 @@ and shift, so it is the same alone and in any mix.
 
 Completion times are measured on the device (CUDA events relative to one
 start event); latency = completion of the request's last chunk - arrival.
-FP32 requests above the FP32 handle's order limit run on the FP64 handle and
-are rounded to FP32 at the end.
+FP32 requests are computed in FP32 up to order FP32_MAX_ORDER and otherwise on
+the FP64 handle, rounded to FP32 at the end: the rotation path in FP32 stays
+within the 1e-5 FP32 tolerance up to order 12 (its rounding grows through
+the four swaps; at order 16 single targets reach 1e-4), and FP32 storage of an
+FP64 result is within it at every order.
 """
 import math
 import time
@@ -30,6 +33,7 @@ from . import sfmm
 from . import workloads as W
 
 OPS = ("m2m", "m2l", "l2l")
+FP32_MAX_ORDER = 12          # highest order computed in FP32 (see the module notes)
 
 
 @dataclass
@@ -101,7 +105,7 @@ class TranslationServer:
                  n_streams=4, chunk=32768, inflight_per_stream=2, device="cuda", seed=5):
         self.device = torch.device(device)
         self.P_max = P_max
-        self.P32 = min(P_max, 29)
+        self.P32 = min(P_max, FP32_MAX_ORDER)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(n_streams)]
         # one handle per stream and dtype: launches that use a handle's global
         # scratch run one after another, so streams with their own handles overlap

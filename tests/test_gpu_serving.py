@@ -63,5 +63,5 @@ def test_served_results_match_oracle(server, orc):
             sh = sh.astype(np.float32).astype(np.float64)
         want, _ = orc.batch(r.op, r.p_in, r.p_out, src, sh)
         got = r.out.double().cpu().numpy()[i]
-        tol = 1e-12 if r.dtype == "f64" else 1e-4
+        tol = 1e-12 if r.dtype == "f64" else 1e-5
         assert U.rel_err(got, want, r.p_out, U.out_kind(r.op)) <= tol, (r.rid, r.op, r.dtype, r.p_in, r.p_out)
