@@ -10,7 +10,9 @@ the M2M-combined multipoles of its children at the same order).
   locals (the lists kernels add in a fixed order).
 * The same tree at P = 16 through the tensor-core grid M2L of level 5
   (three-part BF16 split, FP64 target sums): 3 sampled targets at the FP32-class
-  tolerance."""
+  tolerance.
+* The largest serving request (10^6 M2L, FP64 at order 30, FP32 at order 12).
+* The mixed-order pass on the 2 M-point Plummer sphere: 3 sampled targets."""
 import numpy as np
 import pytest
 
@@ -114,4 +116,81 @@ def test_grid_level5_p16_sampled_against_oracle(sf, orc, tree):
         want = _oracle_m2l(orc, tree, DEPTH, t, P, cache)
         assert U.rel_err(got[t], want, P, "L") <= 1e-5, t
     grid.close()
+    h.close()
+
+
+@pytest.mark.parametrize("dtype,P", [("f64", 30), ("f32", 12)])
+def test_batch_m2l_one_million_sampled_against_oracle(sf, orc, dtype, P):
+    """The largest request of the serving mix: 10^6 M2L of the highest order
+    the dtype computes (FP32 above order 12 is computed in FP64 by the server),
+    from a resident pool of 4,096 P2M solids and 2^16 shifts."""
+    import torch
+    g = W.rng(500 + P)
+    n, pool = 1_000_000, 4096
+    S = P * (P + 1)
+    pos, q = W.charge_clusters(g, pool, 32)
+    C = np.stack([orc.p2m(P, pos[i], q[i], np.zeros(3)) for i in range(pool)])
+    sh = W.shifts(g, 1 << 16, 2.0, 4.0)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    if dtype == "f32":
+        C, sh = C.astype(np.float32).astype(np.float64), sh.astype(np.float32).astype(np.float64)
+    h = sf.Handle(P, dtype)
+    dC = torch.tensor(C, dtype=tdt, device="cuda")
+    dsh = torch.tensor(sh, dtype=tdt, device="cuda")
+    out = torch.empty(n, S, dtype=tdt, device="cuda")
+    idx = torch.arange(n)
+    pin = sf.pointer_array(dC, S, idx % pool)
+    pout = sf.pointer_array(out, S, idx)
+    shifts = dsh[torch.arange(n, device="cuda") % (1 << 16)].contiguous()
+    sf.m2l_batch(h, pin, pout, shifts, P, P, n)
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    picks = np.sort(g.choice(n, size=6, replace=False))
+    got = out[torch.tensor(picks, device="cuda")].double().cpu().numpy()
+    want, _ = orc.batch("m2l", P, P, C[picks % pool], sh[picks % (1 << 16)])
+    tol = 1e-12 if dtype == "f64" else 1e-5
+    assert U.rel_err(got, want, P, "L") <= tol
+    h.close()
+
+
+def test_adaptive_plummer_2m_sampled_against_oracle(sf, orc):
+    """The mixed-order pass on the 2 M-point Plummer sphere (orders 4-24 rising
+    with the level, dual-tree M2L): upward pass and all M2L waves as fused
+    multi-class launches with the default policies; 3 sampled targets of the
+    largest wave, summed over every wave, against the oracle (each source's
+    multipole by P2M of its own points at its own order)."""
+    import torch
+    from paper_2202_02847_gb300.fmm import AdaptivePass
+    pts, q = W.plummer(1 << 21, seed=4)
+    tree = W.adaptive_octree(pts, leaf_size=64)
+    P_node = np.asarray(W.order_by_level(tree, lo=4, span=20))
+    h = sf.Handle(int(P_node.max()), "f64")
+    ap = AdaptivePass(tree, P_node, h)
+    ap.p2m_leaves(pts, q)
+    ap.upward()
+    ap.L.zero_()
+    ap.m2l_all()
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    L = ap.L.cpu().numpy()
+    big = max(range(len(ap.waves)), key=lambda w: len(ap.waves[w]["host"]["src"]))
+    g = W.rng(79)
+    rows = ap.waves[big]["host"]
+    lens = np.diff(rows["offs"])
+    cand = rows["row_tgt"][lens >= 32]
+    Mcache = {}
+    for t in g.choice(cand, size=3, replace=False):
+        Po = int(P_node[t])
+        want = np.zeros(Po * (Po + 1))
+        for d in ap.waves:
+            hst = d["host"]
+            for r in np.nonzero(hst["row_tgt"] == t)[0]:
+                for j in range(hst["offs"][r], hst["offs"][r + 1]):
+                    s = int(hst["src"][j])
+                    if s not in Mcache:
+                        sel = tree.order[tree.pt_begin[s]:tree.pt_end[s]]
+                        Mcache[s] = orc.p2m(int(P_node[s]), pts[sel], q[sel], tree.centre[s])
+                    want += orc.translate("m2l", int(P_node[s]), Po, Mcache[s], tree.centre[t] - tree.centre[s])
+        got = L[ap.off[t]:ap.off[t + 1]]
+        assert U.rel_err(got, want, Po, "L") <= 1e-12, t
     h.close()
