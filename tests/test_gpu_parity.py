@@ -355,3 +355,39 @@ def test_lists_multi_rejects_bad_lanes(sf, h64):
     z = torch.zeros(2, dtype=torch.int64, device="cuda")
     with pytest.raises(sf.SfmmError):
         sf.translate_lists_multi(h64, [("m2l", 4, 4, 0, 1, 3)], z, z, z, z)
+
+
+def test_lists_on_two_streams_share_one_handle(sf, h64):
+    """Group-lists launches of one handle on two streams use its one scratch
+    and chunk counter; the handle orders them, so each result is bitwise the
+    one computed alone."""
+    import torch
+    g = W.rng(6200)
+    P = 14
+    S = P * (P + 1)
+    res = []
+    cases = []
+    for k in range(2):
+        nt = 300
+        lens = g.integers(1, 60, size=nt)
+        offs = np.zeros(nt + 1, np.int64)
+        np.cumsum(lens, out=offs[1:])
+        C = torch.tensor(W.random_solids(g, 128, P), device="cuda")
+        src = sf.pointer_array(C, S, torch.tensor(g.integers(0, 128, size=int(offs[-1]))))
+        sh = torch.tensor(W.shifts(g, int(offs[-1])), device="cuda")
+        cases.append((C, src, sh, torch.tensor(offs, device="cuda"), nt))
+    for C, src, sh, offs, nt in cases:                  # alone, one after the other
+        out = torch.zeros(nt, S, dtype=torch.float64, device="cuda")
+        sf.translate_lists(h64, "m2l", src, sh, offs, sf.pointer_array(out, S, torch.arange(nt)), P, P, nt)
+        torch.cuda.synchronize()
+        res.append(out)
+    streams = [torch.cuda.Stream() for _ in cases]
+    outs = [torch.zeros(nt, S, dtype=torch.float64, device="cuda") for *_, nt in cases]
+    ptrs = [sf.pointer_array(o, S, torch.arange(o.shape[0])) for o in outs]
+    torch.cuda.synchronize()                            # inputs ready before either stream starts
+    for (C, src, sh, offs, nt), s, po in zip(cases, streams, ptrs):
+        sf.translate_lists(h64, "m2l", src, sh, offs, po, P, P, nt, stream=s)
+    torch.cuda.synchronize()
+    assert h64.sync_status() == 0
+    for a, b in zip(outs, res):
+        assert torch.equal(a, b)
