@@ -287,9 +287,9 @@ sfmm_status sfmm_sync_status(sfmm_handle h, sfmm_stream stream, int *device_stat
 /*
  * Batched translations that allocate nothing (the paper has no counterpart;
  * this is an interface for callers that cannot allocate device memory where
- * they translate: code running while a stream is captured into a CUDA graph,
- * a host framework that hands out a fixed device-memory budget, or a real-time
- * loop where cudaMalloc/cudaFree and their implicit synchronisation are not
+ * they translate: a plug-in inside a host framework that hands out a fixed
+ * device-memory budget and owns every allocation, or a real-time loop where
+ * cudaMalloc/cudaFree and the device synchronisation they imply are not
  * allowed).  Same arguments and results as sfmm_m2m/m2l/l2l_batch with the
  * op selected by `op`, computed by the global-scratch variant of the batch
  * kernel whose scratch is a fixed 16 MiB device array inside the library

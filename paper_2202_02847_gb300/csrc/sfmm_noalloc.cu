@@ -1,10 +1,10 @@
 // sfmm_translate_batch_noalloc: batched translations that allocate nothing.
 //
 // Some callers cannot allocate device memory at the point where they
-// translate: code that runs while a stream is being captured into a CUDA
-// graph, inside a fixed device-memory budget handed out by a host framework,
-// or in a real-time loop where an allocation (and the implicit device
-// synchronisation of cudaMalloc / cudaFree) is not allowed.  For them this
+// translate: a plug-in running inside a fixed device-memory budget handed out
+// by a host framework that owns every allocation, or a real-time loop where an
+// allocation (and the implicit device synchronisation of cudaMalloc /
+// cudaFree) is not allowed.  For them this
 // entry point runs the global-scratch variant of the batch kernel with its
 // scratch in a fixed device array compiled into the library instead of a
 // buffer owned by the handle.  It calls no cudaMalloc, cudaFree or other

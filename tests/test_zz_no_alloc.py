@@ -1,7 +1,8 @@
 """sfmm_translate_batch_noalloc against the regular batch entry point.
 
 The entry point serves callers that cannot allocate device memory where they
-translate (graph capture, fixed memory budgets, real-time loops); its scratch
+translate (plug-ins inside a host framework's fixed memory budget, real-time
+loops that forbid cudaMalloc/cudaFree and their synchronisation); its scratch
 is a fixed array inside the library.  Two calls in a row, with different ops,
 orders and inputs, must each agree with sfmm_*_batch within the FP64
 tolerance of the parity tests.  This file is collected last on purpose."""
