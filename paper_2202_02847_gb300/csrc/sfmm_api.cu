@@ -85,8 +85,8 @@ sfmm_status fill_unrolled_constants(int dev, size_t smem_optin) {
     std::lock_guard<std::mutex> lk(g_const_mu);
     if (g_const_filled[dev]) return SFMM_OK;
     HostTables ht;
-    // layout of sfmm_unrolled.cuh: packed F and G of rows n < PC, c, 1/c and the
-    // three z-translation block sets, all built for order PC
+    // layout of sfmm_unrolled.cuh: packed F and G of rows n < PC, c, 1/c, the
+    // three z-translation block sets and M2L's folded swaps, all built for order PC
     if (build_tables(unrolled::PC, &ht) != 0) return SFMM_ERR_ORDER;
     std::vector<double> t;
     const int nF = unrolled::FR(unrolled::PC), nG = unrolled::GR(unrolled::PC);
@@ -95,6 +95,30 @@ sfmm_status fill_unrolled_constants(int dev, size_t smem_optin) {
     t.insert(t.end(), ht.c.begin(), ht.c.end());
     t.insert(t.end(), ht.ic.begin(), ht.ic.end());
     for (int op = 0; op < 3; ++op) t.insert(t.end(), ht.Tz[op].begin(), ht.Tz[op].end());
+    // M2L's swaps with the basis factors folded in: F diag(c), G diag(c) (first
+    // input swap), then diag(c) F, diag(c) G (last output swap)
+    std::vector<double> fi(nF), gi(nG), fo(nF), go(nG);
+    for (int n = 0; n < unrolled::PC; ++n) {
+        if (ht.Frow[n] != unrolled::FR(n) || ht.Grow[n] != unrolled::GR(n)) return SFMM_ERR_UNSUPPORTED;
+        const double *cn = ht.c.data() + n * (n + 1) / 2;
+        for (int m = 0; m <= n; ++m) {
+            int i = unrolled::FR(n) + unrolled::FM(n, m);
+            for (int l = (n + m) & 1; l <= n; l += 2, ++i) {
+                fi[i] = ht.F[i] * cn[l];
+                fo[i] = cn[m] * ht.F[i];
+            }
+            if (m == 0) continue;
+            int j = unrolled::GR(n) + unrolled::GM(n, m);
+            for (int l = unrolled::l0G(n, m); l <= n; l += 2, ++j) {
+                gi[j] = ht.G[j] * cn[l];
+                go[j] = cn[m] * ht.G[j];
+            }
+        }
+    }
+    t.insert(t.end(), fi.begin(), fi.end());
+    t.insert(t.end(), gi.begin(), gi.end());
+    t.insert(t.end(), fo.begin(), fo.end());
+    t.insert(t.end(), go.begin(), go.end());
     if ((int)t.size() != unrolled::table_size()) return SFMM_ERR_UNSUPPORTED;
     std::vector<float> t32(t.begin(), t.end());
     if (!unrolled::fill_constants(t.data(), t32.data())) return SFMM_ERR_CUDA;

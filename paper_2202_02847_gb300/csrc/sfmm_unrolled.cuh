@@ -76,7 +76,15 @@ constexpr int OFF_G = OFF_F + FR(PC);
 constexpr int OFF_C = OFF_G + GR(PC);
 constexpr int OFF_IC = OFF_C + PC * (PC + 1) / 2;
 constexpr int OFF_T = OFF_IC + PC * (PC + 1) / 2;
-constexpr int NTAB = OFF_T + 3 * QT(PC);
+// M2L only: the basis factors c folded into the swap next to them, F diag(c)
+// and G diag(c) for the first input swap, diag(c) F and diag(c) G for the
+// last output swap (same packing as F and G), which saves one multiply per
+// coefficient on either side.
+constexpr int OFF_FI = OFF_T + 3 * QT(PC);
+constexpr int OFF_GI = OFF_FI + FR(PC);
+constexpr int OFF_FO = OFF_GI + GR(PC);
+constexpr int OFF_GO = OFF_FO + FR(PC);
+constexpr int NTAB = OFF_GO + GR(PC);
 
 // One copy per translation unit (each unit is its own module); filled by
 // fill_constants() of that unit.
@@ -108,8 +116,9 @@ struct Sw {
     __device__ __forceinline__ T &at(int e, int j) const { return wb[e * XSTRIDE + j]; }
 };
 
-// One axis swap of row N (eq. Mswapxz / FGmappings) on register rows.
-template <typename T, int N>
+// One axis swap of row N (eq. Mswapxz / FGmappings) on register rows, with
+// the packed F and G found at table offsets OF and OG.
+template <typename T, int N, int OF = OFF_F, int OG = OFF_G>
 __device__ __forceinline__ void swap_u(const T *ir, const T *ii, T *orr, T *oi) {
 #pragma unroll
     for (int m = 0; m <= N; ++m) {
@@ -117,7 +126,7 @@ __device__ __forceinline__ void swap_u(const T *ir, const T *ii, T *orr, T *oi) 
         int i = 0;
 #pragma unroll
         for (int l = (N + m) & 1; l <= N; l += 2, ++i)
-            acc = fma_t(ct<T>(OFF_F + FR(N) + FM(N, m) + i), ir[l], acc);
+            acc = fma_t(ct<T>(OF + FR(N) + FM(N, m) + i), ir[l], acc);
         orr[m] = acc;
     }
     oi[0] = T(0);
@@ -127,7 +136,7 @@ __device__ __forceinline__ void swap_u(const T *ir, const T *ii, T *orr, T *oi) 
         int i = 0;
 #pragma unroll
         for (int l = l0G(N, m); l <= N; l += 2, ++i)
-            acc = fma_t(ct<T>(OFF_G + GR(N) + GM(N, m) + i), ii[l], acc);
+            acc = fma_t(ct<T>(OG + GR(N) + GM(N, m) + i), ii[l], acc);
         oi[m] = acc;
     }
 }
@@ -144,14 +153,23 @@ __device__ __forceinline__ void rows_in(Sw<T> X, const Powers<T, P> &pw, T s, T 
     if constexpr (N < P) {
         constexpr int o = N * (N + 1);
         T ar[N + 1], ai[N + 1], br[N + 1], bi[N + 1];
+        // M2L: the basis factor is folded into the first swap's tables.
+        // m = 0: the rotation is the identity and Im C_n^0 is not read by the
+        // swap (its G rows start at l >= 1).
 #pragma unroll
         for (int m = 0; m <= N; ++m) {
-            const T f = s * ct<T>((OP == OP_L2L ? OFF_IC : OFF_C) + N * (N + 1) / 2 + m);
+            const T f = (OP == OP_M2L) ? s : s * ct<T>((OP == OP_L2L ? OFF_IC : OFF_C) + N * (N + 1) / 2 + m);
+            if (m == 0) {
+                ar[0] = X[o] * f;
+                ai[0] = T(0);
+                continue;
+            }
             const T re = X[o + m] * f, im = X[o + N + 1 + m] * f;
             ar[m] = re * pw.ar[m] - im * pw.ai[m];
             ai[m] = fma_t(re, pw.ai[m], im * pw.ar[m]);
         }
-        swap_u<T, N>(ar, ai, br, bi);
+        if constexpr (OP == OP_M2L) swap_u<T, N, OFF_FI, OFF_GI>(ar, ai, br, bi);
+        else swap_u<T, N>(ar, ai, br, bi);
 #pragma unroll
         for (int m = 1; m <= N; ++m) {
             const T re = br[m], im = bi[m];
@@ -203,10 +221,18 @@ __device__ __forceinline__ void rows_out(Sw<T> X, const Powers<T, P> &pw, T so, 
             br[m] = fma_t(re, pw.br[m], im * pw.bi[m]);
             bi[m] = im * pw.br[m] - re * pw.bi[m];
         }
-        swap_u<T, N>(br, bi, ar, ai);
+        // M2L: the basis factor is folded into the last swap's tables.
+        // m = 0: the rotation is the identity and the swap leaves Im = 0.
+        if constexpr (OP == OP_M2L) swap_u<T, N, OFF_FO, OFF_GO>(br, bi, ar, ai);
+        else swap_u<T, N>(br, bi, ar, ai);
 #pragma unroll
         for (int m = 0; m <= N; ++m) {
-            const T f = so * ct<T>((OP == OP_M2M ? OFF_IC : OFF_C) + N * (N + 1) / 2 + m);
+            const T f = (OP == OP_M2L) ? so : so * ct<T>((OP == OP_M2M ? OFF_IC : OFF_C) + N * (N + 1) / 2 + m);
+            if (m == 0) {
+                X[o] = ar[0] * f;
+                X[o + N + 1] = T(0);
+                continue;
+            }
             const T re = ar[m] * f, im = ai[m] * f;
             X[o + m] = fma_t(re, pw.ar[m], im * pw.ai[m]);
             X[o + N + 1 + m] = im * pw.ar[m] - re * pw.ai[m];
@@ -240,8 +266,9 @@ __device__ __forceinline__ void translate_u(Sw<T> X, T x, T y, T z) {
     const T cb = z * iR, sb = -rho * iR;                  // cos(beta) = z/|r|, sin(beta) = -rho/|r|
     Powers<T, P> pw;
     pw.ar[0] = T(1); pw.ai[0] = T(0); pw.br[0] = T(1); pw.bi[0] = T(0);
+    if constexpr (P > 1) { pw.ar[1] = ca; pw.ai[1] = sa; pw.br[1] = cb; pw.bi[1] = sb; }
 #pragma unroll
-    for (int m = 1; m < P; ++m) {
+    for (int m = 2; m < P; ++m) {
         pw.ar[m] = pw.ar[m - 1] * ca - pw.ai[m - 1] * sa;
         pw.ai[m] = fma_t(pw.ar[m - 1], sa, pw.ai[m - 1] * ca);
         pw.br[m] = pw.br[m - 1] * cb - pw.bi[m - 1] * sb;
