@@ -240,6 +240,7 @@ __device__ __forceinline__ void rows_out(Sw<T> X, const Powers<T, P> &pw, T so, 
     }
 }
 
+// One row or column per step.
 template <typename T, int P, int OP, int K>
 __device__ __forceinline__ void step_switch(int st, Sw<T> X, const Powers<T, P> &pw, T s, T so) {
     if constexpr (K < 3 * P) {
@@ -253,8 +254,38 @@ __device__ __forceinline__ void step_switch(int st, Sw<T> X, const Powers<T, P> 
     }
 }
 
+// Paired steps: rows n and P-1-n (columns M and P-1-M) share one step, so
+// every step carries about the same work, (n+1)^2 + (P-n)^2 multiply-adds,
+// and two independent sets of FMA chains for the scheduler to interleave.
+// Only the M2L lists kernel pairs its steps: the batch kernels and the M2M and
+// L2L lists kernels have no registers to spare for a second row and the row
+// scales of every row (they would spill).
+template <typename T, int P, int OP, int K>
+__device__ __forceinline__ void step_switch2(int st, Sw<T> X, const Powers<T, P> &pw, const T *sin,
+                                             const T *sout) {
+    constexpr int H = (P + 1) / 2;
+    if constexpr (K < 3 * H) {
+        if (st == K) {
+            constexpr int ph = K / H, i = K % H, j = P - 1 - i;
+            if constexpr (ph == 0) {
+                rows_in<T, P, OP, i>(X, pw, sin[i], T(0));
+                if constexpr (j != i) rows_in<T, P, OP, j>(X, pw, sin[j], T(0));
+            } else if constexpr (ph == 1) {
+                columns_z<T, P, OP, i>(X);
+                if constexpr (j != i) columns_z<T, P, OP, j>(X);
+            } else {
+                rows_out<T, P, OP, i>(X, pw, sout[i], T(0));
+                if constexpr (j != i) rows_out<T, P, OP, j>(X, pw, sout[j], T(0));
+            }
+        } else {
+            step_switch2<T, P, OP, K + 1>(st, X, pw, sin, sout);
+        }
+    }
+}
+
 // One translation of order P by the calling thread, in place on its solid X.
-template <typename T, int P, int OP>
+// PAIRED (M2L in the lists kernel) runs two rows or columns per step.
+template <typename T, int P, int OP, bool PAIRED = false>
 __device__ __forceinline__ void translate_u(Sw<T> X, T x, T y, T z) {
     const T rho2 = x * x + y * y;
     const T R = sqrt_t(rho2 + z * z);
@@ -274,18 +305,31 @@ __device__ __forceinline__ void translate_u(Sw<T> X, T x, T y, T z) {
         pw.br[m] = pw.br[m - 1] * cb - pw.bi[m - 1] * sb;
         pw.bi[m] = fma_t(pw.br[m - 1], sb, pw.bi[m - 1] * cb);
     }
-    // One basic block per row / column step: a runtime loop over the steps
-    // with a switch keeps the instruction scheduler from interleaving steps
-    // (which would keep several rows of tables and data alive at once).
-    T s = (OP == OP_M2L) ? iR : T(1);                   // input scale |r|^{-(n+1)}, ^{-n}, ^{n}
+    // Row scales: input |r|^{-(n+1)} (M2L), |r|^{-n} (M2M), |r|^{n} (L2L);
+    // output |r|^{-n} (M2L, L2L), |r|^{n} (M2M).
+    const T s0 = (OP == OP_M2L) ? iR : T(1);
     const T step_in = (OP == OP_L2L) ? R : iR;
-    T so = T(1);                                       // output scale
     const T step_out = (OP == OP_M2M) ? R : iR;
+    // One basic block per row or column step (or pair of them): a runtime loop
+    // over the steps with a switch keeps the instruction scheduler from
+    // interleaving more steps (which would keep more rows of tables and data
+    // alive at once).
+    if constexpr (PAIRED) {
+        T sin[P], sout[P];
+        sin[0] = s0;
+        sout[0] = T(1);
+#pragma unroll
+        for (int n = 1; n < P; ++n) { sin[n] = sin[n - 1] * step_in; sout[n] = sout[n - 1] * step_out; }
 #pragma unroll 1
-    for (int st = 0; st < 3 * P; ++st) {
-        step_switch<T, P, OP, 0>(st, X, pw, s, so);
-        if (st < P) s *= step_in;
-        else if (st >= 2 * P) so *= step_out;
+        for (int st = 0; st < 3 * ((P + 1) / 2); ++st) step_switch2<T, P, OP, 0>(st, X, pw, sin, sout);
+    } else {
+        T s = s0, so = T(1);
+#pragma unroll 1
+        for (int st = 0; st < 3 * P; ++st) {
+            step_switch<T, P, OP, 0>(st, X, pw, s, so);
+            if (st < P) s *= step_in;
+            else if (st >= 2 * P) so *= step_out;
+        }
     }
 }
 
@@ -390,7 +434,7 @@ __global__ void __launch_bounds__(256, 1) ulists_kernel(const T *const *src, con
             __syncwarp();
             T x = T(0), y = T(0), z = T(1);
             if (s) { x = shift[3 * j]; y = shift[3 * j + 1]; z = shift[3 * j + 2]; }
-            translate_u<T, P, OP>(X, x, y, z);
+            translate_u<T, P, OP, OP == OP_M2L>(X, x, y, z);
             __syncwarp();
 #pragma unroll
             for (int a = 0; a < NA; ++a) {
