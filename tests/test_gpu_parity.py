@@ -228,9 +228,46 @@ def test_lists_fixed_orders(sf, orc, h64, op, accumulate, P):
 
 
 @pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
-def test_lists_fixed_orders_fp32(sf, orc, h32, op):
-    err = _run_lists(sf, orc, h32, op, 10, 10, False, 6200, dtype="f32")
+@pytest.mark.parametrize("P", [6, 8, 10, 12])
+def test_lists_fixed_orders_fp32(sf, orc, h32, op, P):
+    err = _run_lists(sf, orc, h32, op, P, P, False, 6200 + P, dtype="f32")
     assert err <= TOL["f32"], err
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("P", [6, 8, 10, 12])
+def test_lists_m2l_special_shifts(sf, orc, h64, h32, dtype, P):
+    """The interaction-list M2L kernel (paired row and column steps, basis
+    factors folded into its swap tables) on shifts along +z and -z (rho = 0,
+    Sec. 3.4 step 1), nearly axial and axis-aligned shifts, each target
+    summing a list of all of them."""
+    import torch
+    h = h64 if dtype == "f64" else h32
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    base = np.array([[0, 0, 3.0], [0, 0, -2.5], [1e-170, 0, 3.0], [0, 1e-9, -2.2],
+                     [3.0, 0, 0], [0, -2.4, 0], [2.0, 2.0, 0], [-1.5, 0, 1.5]])
+    if dtype == "f32":
+        base[2, 0] = 1e-30                          # representable in FP32
+    g = W.rng(6300 + P)
+    nt, per = 40, len(base)
+    S = W.random_solids(g, nt * per, P)
+    sh = np.tile(base, (nt, 1))
+    if dtype == "f32":
+        S, sh = (a.astype(np.float32).astype(np.float64) for a in (S, sh))
+    offs = np.arange(0, nt * per + 1, per, dtype=np.int64)
+    dS = torch.tensor(S, device="cuda", dtype=tdt)
+    dO = torch.zeros(nt, P * (P + 1), device="cuda", dtype=tdt)
+    psrc = sf.pointer_array(dS, P * (P + 1), torch.arange(nt * per))
+    pout = sf.pointer_array(dO, P * (P + 1), torch.arange(nt))
+    sf.translate_lists(h, "m2l", psrc, torch.tensor(sh, device="cuda", dtype=tdt),
+                       torch.tensor(offs, device="cuda"), pout, P, P, nt)
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    got = dO.double().cpu().numpy()
+    each, _ = orc.batch("m2l", P, P, S, sh)
+    want = each.reshape(nt, per, -1).sum(axis=1)
+    err = U.rel_err(got, want, P, U.out_kind("m2l"))
+    assert err <= TOL[dtype], err
 
 
 @pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
