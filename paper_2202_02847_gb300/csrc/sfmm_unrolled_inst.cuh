@@ -57,6 +57,18 @@ bool geometry(K kernel, const Launch &L, long long chunks, int *warps, size_t *s
         if (nb > 0 && w * nb > best_w * best_nb) { best_w = w; best_nb = nb; }
     }
     if (best_w < 1) { best_w = wmax; best_nb = 1; }
+    // Small launches (no more warp-chunks than sub-partitions): blocks of at
+    // most 4 warps, one warp per sub-partition.  The FP64 pipe of a
+    // sub-partition is shared by its warps, so two warps of a small tree
+    // level on one sub-partition take twice as long as on two.
+    if (chunks <= 4LL * L.sm_count && best_w > 4) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, 4 * 32, (size_t)4 * per_warp) == cudaSuccess &&
+            nb > 0) {
+            best_w = 4;
+            best_nb = nb;
+        }
+    }
     *warps = best_w;
     *smem = (size_t)best_w * per_warp;
     const long long b = (chunks + best_w - 1) / best_w;
