@@ -91,8 +91,11 @@ const char *sfmm_status_string(sfmm_status s);
  *     Fig. 2) and packed without their structural zeros;
  *   - the z-axis translation matrices of M2L (eq. zm2l-matrix, factorials),
  *     M2M and L2L in the same basis.
- * 1 <= P_max <= 64 for SFMM_F64; 1 <= P_max <= 29 for SFMM_F32 (the FP32
- * range of the basis factors sqrt((n-m)!(n+m)!)).  Also allocates the
+ * 1 <= P_max <= 64 for SFMM_F64; 1 <= P_max <= 30 for SFMM_F32 (the orders
+ * of the paper's workloads; FP32 coefficients of unit-sized boxes stay in
+ * range there, whereas coefficients of boxes much smaller or larger than the
+ * shift unit leave the FP32 range at high order whatever the algorithm, since
+ * R_n^m ~ r^n / (n+m)! and S_n^m ~ (n-m)!/r^(n+1)).  Also allocates the
  * handle's global scratch (see sfmm_reserve_scratch): 2 P_max (P_max + 1)
  * reals per lane for 8 warps per SM, e.g. 29 MB at P_max = 10 and 1.3 GB at
  * P_max = 64 in FP64 on 152 SMs.  Synchronous.
@@ -203,7 +206,11 @@ sfmm_status sfmm_translate_lists_multi(sfmm_handle h, const sfmm_list_class *cla
  *                          memory while two blocks of two or more warps fit
  *                          per SM; else the global scratch (launches that use
  *                          the scratch of one handle run one after another,
- *                          whatever their streams)
+ *                          whatever their streams, through an event of the
+ *                          handle; launches captured into a CUDA graph skip
+ *                          that event, so a captured graph is not ordered
+ *                          against other work on the same handle: give each
+ *                          graph a handle of its own)
  *   SFMM_POLICY_UNROLLED - fixed-order kernel; only p_in = p_out in {6,8,10,12}
  *   SFMM_POLICY_SHARED   - generic kernel, working set in shared memory
  *   SFMM_POLICY_GLOBAL   - generic kernel, rotated solid in the global scratch
@@ -249,7 +256,9 @@ sfmm_status sfmm_reserve_scratch(sfmm_handle h, int p_in_max);
  * per target; results agree with the FP64 rotation path to about 3e-6, every
  * target within 1e-5 (weighted coefficient error).  Asynchronous on
  * `stream`; one call at a time per grid object.  A device-side wait that gives
- * up sets bit 4 of the handle's status word (sfmm_sync_status).
+ * up sets bit 4 of the handle's status word (sfmm_sync_status); bit 8 means
+ * that, after such a time-out, copies or MMAs already issued did not finish
+ * within 2 s either (the kernel then keeps its tensor memory allocated).
  * Errors: SFMM_ERR_ARG, SFMM_ERR_ORDER (handle not FP64 or P_max < 16),
  * SFMM_ERR_UNSUPPORTED (P != 16), SFMM_ERR_NOMEM, SFMM_ERR_CUDA.
  */

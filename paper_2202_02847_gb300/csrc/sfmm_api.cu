@@ -1,6 +1,7 @@
 // C ABI of the translation library: handle, argument validation, launches.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -22,7 +23,7 @@ static_assert(SFMM_MAX_CLASSES == MAX_CLASSES, "class table sizes of the ABI and
 namespace {
 
 constexpr int kMaxPmax64 = 64;
-constexpr int kMaxPmax32 = 29;
+constexpr int kMaxPmax32 = 30;
 
 template <typename T>
 void set_kernel_attrs(size_t smem) {
@@ -50,7 +51,16 @@ sfmm_status upload(const HostTables &ht, sfmm_ctx *h, DevTables<T> *dt) {
         o += v.size();
         return at;
     };
-    const size_t oF = put(ht.F), oG = put(ht.G), oc = put(ht.c), oic = put(ht.ic);
+    // FP32: c_n^m 2^-n and 2^n / c_n^m, which stay inside the FP32 range up to
+    // order 30 (the kernels multiply the row's 2^{+-n} back in, basis_factor)
+    std::vector<double> cs = ht.c, ics = ht.ic;
+    if (sizeof(T) == sizeof(float))
+        for (int n = 0; n < ht.Pmax; ++n)
+            for (int m = 0; m <= n; ++m) {
+                cs[n * (n + 1) / 2 + m] = std::ldexp(ht.c[n * (n + 1) / 2 + m], -n);
+                ics[n * (n + 1) / 2 + m] = std::ldexp(ht.ic[n * (n + 1) / 2 + m], n);
+            }
+    const size_t oF = put(ht.F), oG = put(ht.G), oc = put(cs), oic = put(ics);
     const size_t oT0 = put(ht.Tz[0]), oT1 = put(ht.Tz[1]), oT2 = put(ht.Tz[2]);
     size_t ibyte = (o * sizeof(T) + 15) / 16 * 16;
     int *ip = reinterpret_cast<int *>(host.data() + ibyte);

@@ -58,7 +58,8 @@ constexpr int FLUSH = 2;           // offsets accumulated in FP32 before an FP64
 constexpr int NU = 189;            // offsets of a child octant
 constexpr int NCH_ALL = NU * NKC;  // K chunks of a tile
 constexpr int NCODE = 343;         // offset codes ((dx+3)*7 + dy+3)*7 + dz+3
-constexpr int STATUS_GRID_TIMEOUT = 4;
+constexpr int STATUS_GRID_TIMEOUT = 4;       // a pipeline wait gave up
+constexpr int STATUS_GRID_DRAIN = 8;         // work in flight did not finish within 2 s
 
 // reduced real layout of a solid of order GP: row n at n^2: Re m=0..n, Im m=1..n
 __host__ __device__ inline void reduced_index(int e, int *n, int *m, bool *im) {
@@ -238,6 +239,20 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, vol
     return false;
 }
 
+// bounded wait for work already issued (the drains before the CTA frees its
+// shared and tensor memory): it ignores the abort flag, because copies and
+// MMAs in flight complete whether or not another role has given up, and stops
+// after 2 s (or 2^24 polls)
+__device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity) {
+    if (try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (int it = 1; it < (1 << 24); ++it) {
+        if (try_wait(bar, parity)) return true;
+        if ((it & 255) == 0 && global_ns() - t0 > 2000000000ull) return false;
+    }
+    return false;
+}
+
 // Work units: (K slab, tile) pairs in slab-major order, a slab being the K
 // chunks of GW consecutive chunks (FLUSH offsets) of a tile; one unit is one
 // FP32 accumulation group.  CTA c takes units c, c + G, c + 2G, ... so that at
@@ -268,8 +283,10 @@ constexpr int smem_gemm() { return NST * (NPART * A_PART + NPART * NT * KC * 2) 
 //     and arrive on `acc_empty`, which the MMA thread waits on before it reuses
 //     the buffer.  The epilogue of one unit overlaps the MMAs of the next.
 // Every wait is bounded; a time-out sets the abort flag and the status word,
-// the other roles give up their waits, the copy and MMA threads wait (bounded)
-// for their work in flight, and the CTA frees its tensor memory and returns.
+// the other roles give up their waits, the copy and MMA threads wait for their
+// work in flight (bounded by time only, whatever the abort flag says), and the
+// CTA frees its tensor memory and returns; if that drain also runs out, bit 8
+// of the status word is set and the tensor memory is kept.
 template <int NT>
 __global__ void __launch_bounds__(192, 1)
 grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_mid,
@@ -285,6 +302,7 @@ grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __
     uint64_t *acc_empty = acc_full + 2;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(acc_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    volatile int *drain_failed = abort_flag + 1;
     int *codes = reinterpret_cast<int *>(sm + NST * STAGE + 1024);   // [8][NU]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ns = a.nside, half_ns = ns / 2, tpd = half_ns / 4, tpz = half_ns / TZ;
@@ -308,6 +326,7 @@ grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
         *abort_flag = 0;
+        *drain_failed = 0;
     }
     if (tid >= 64 && tid < 72) {
         // octant o: offsets u = target - source with u_i in [-3 + b_i, 2 + b_i], max|u_i| >= 2
@@ -328,6 +347,10 @@ grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __
     auto fail = [&]() {
         *abort_flag = 1;
         atomicOr(a.status, STATUS_GRID_TIMEOUT);
+    };
+    auto drain_fail = [&]() {
+        *drain_failed = 1;
+        atomicOr(a.status, STATUS_GRID_DRAIN);
     };
 
     if (warp == 4) {
@@ -378,7 +401,7 @@ grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __
             }
             // drain: every copy issued has landed before the CTA frees its memory
             for (int s = 0; s < NST; ++s)
-                if (last[s] >= 0 && !wait_or_abort(smem_u32(full + s), (uint32_t)((last[s] / NST) & 1), abort_flag)) fail();
+                if (last[s] >= 0 && !wait_bounded(smem_u32(full + s), (uint32_t)((last[s] / NST) & 1))) drain_fail();
         }
         __syncwarp();
     } else if (warp == 5) {
@@ -437,7 +460,7 @@ grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __
                              :: "r"(smem_u32(acc_full + b)) : "memory");
             }
             // drain: the MMAs issued have completed before the CTA frees its memory
-            if (last_mma >= 0 && !wait_or_abort(smem_u32(empty + last_mma % NST), (uint32_t)((last_mma / NST) & 1), abort_flag)) fail();
+            if (last_mma >= 0 && !wait_bounded(smem_u32(empty + last_mma % NST), (uint32_t)((last_mma / NST) & 1))) drain_fail();
         }
         __syncwarp();
     } else {
@@ -491,7 +514,9 @@ grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TCOLS));
+    // tensor memory that MMAs may still write is not freed (status bit 8)
+    if (warp == 0 && !*drain_failed)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TCOLS));
 }
 
 }  // namespace

@@ -23,9 +23,29 @@ struct DevTables {
     const T *F, *G;          // packed reduced swap matrices (see sfmm_tables.h)
     const int *Frow, *Grow;  // row starts, Pmax+1 each
     const T *c, *ic;         // sqrt((n-m)!(n+m)!) and its inverse, n(n+1)/2+m
+                             // (FP32: times 2^-n and 2^n, see row_pow2)
     const T *Tz[3];          // z-axis translation blocks per op
     int Pmax;
 };
+
+// The basis factors leave the FP32 range at order 30 (c_29^29 = sqrt(58!)
+// ~ 1.5e39 > FLT_MAX, 1/c_29^29 is subnormal), although their products with
+// the row scales |r|^{-(n+1)}, |r|^n stay in range for unit-sized boxes.  FP32
+// tables therefore hold c_n^m 2^-n and 2^n / c_n^m, and a row's factor is
+// formed as (scale * table) * 2^{+-n}: the same value as scale * c with one
+// more exact multiplication.  FP64 tables are unscaled (row_pow2 = 1, not
+// issued).
+template <typename T>
+__device__ __forceinline__ T row_pow2(int e) { return T(1); }
+template <>
+__device__ __forceinline__ float row_pow2<float>(int e) {
+    return __int_as_float((127 + e) << 23);            // 2^e, |e| <= 63
+}
+template <typename T>
+__device__ __forceinline__ T basis_factor(T scale, T table, T p2) {
+    if constexpr (sizeof(T) == 4) return (scale * table) * p2;
+    else return scale * table;
+}
 
 // status bits written by kernels (atomicOr into the handle's status word)
 enum { STATUS_NULL_POINTER = 1, STATUS_BAD_OFFSETS = 2 };
@@ -294,10 +314,11 @@ __device__ void translate_impl(const DevTables<T> &tb, int p_in, int p_out,
     for (int n = 0; n < krows; ++n) {
         const T *row = src + n * (n + 1);
         const T *cf = ((OP == OP_L2L) ? tb.ic : tb.c) + n * (n + 1) / 2;
+        const T p2 = row_pow2<T>((OP == OP_L2L) ? -n : n);
         // (b) scale, change to the orthonormal basis, rotate by alpha
         PowSeq<T> pa(ca, sa);
         for (int m = 0; m <= n; ++m) {
-            const T f = s * ldt(cf + m);
+            const T f = basis_factor(s, ldt(cf + m), p2);
             const T re = row[m] * f, im = row[n + 1 + m] * f;
             T pr, pi;
             if constexpr (ptab) { pr = PAre[m]; pi = PAim[m]; } else { pa.next(m, pr, pi); }
@@ -350,10 +371,11 @@ __device__ void translate_impl(const DevTables<T> &tb, int p_in, int p_out,
         swap_row(tb, n, Bre, Bim, Are, Aim, n + 1);
         // rotate by -alpha, undo the scaling and the basis change, store
         const T *cf = ((OP == OP_M2M) ? tb.ic : tb.c) + n * (n + 1) / 2;
+        const T p2 = row_pow2<T>((OP == OP_M2M) ? -n : n);
         D orow = dst + n * (n + 1);
         PowSeq<T> pa(ca, sa);
         for (int m = 0; m <= n; ++m) {
-            const T f = so * ldt(cf + m);
+            const T f = basis_factor(so, ldt(cf + m), p2);
             const T re = Are[m] * f, im = Aim[m] * f;
             T pr, pi;
             if constexpr (ptab) { pr = PAre[m]; pi = PAim[m]; } else { pa.next(m, pr, pi); }

@@ -14,13 +14,13 @@ memory and a stream slot free up and its work overlaps theirs.  Each chunk is
 one C-ABI batch call; a translation's result depends only on its own input
 and shift, so it is the same alone and in any mix.
 
-Completion times are measured on the device (CUDA events relative to one
-start event); latency = completion of the request's last chunk - arrival.
-FP32 requests are computed in FP32 up to order FP32_MAX_ORDER and otherwise on
-the FP64 handle, rounded to FP32 at the end: the rotation path in FP32 stays
-within the 1e-5 FP32 tolerance up to order 12 (its rounding grows through
-the four swaps; at order 16 single targets reach 1e-4), and FP32 storage of an
-FP64 result is within it at every order.
+Arrival and completion are taken on the host clock (completion = when the
+host loop sees the request's last chunk done); latency = completion - arrival.
+Admission is first-fit with an ageing bound, chunks are sized by work, and
+free stream slots serve the request with the least remaining work first.
+FP32 requests are computed by the FP32 handles at every order (the rotation
+path in FP32 keeps every translation of the mix within the 1e-5 FP32
+tolerance up to order 30), FP64 requests by the FP64 handles.
 """
 import math
 import time
@@ -33,7 +33,6 @@ from . import sfmm
 from . import workloads as W
 
 OPS = ("m2m", "m2l", "l2l")
-FP32_MAX_ORDER = 12          # highest order computed in FP32 (see the module notes)
 
 
 @dataclass
@@ -102,18 +101,22 @@ class Arena:
 
 class TranslationServer:
     def __init__(self, P_max=30, pool_size=4096, n_shifts=1 << 20, arena_bytes=8 << 30,
-                 n_streams=4, chunk=32768, inflight_per_stream=2, device="cuda", seed=5):
+                 n_streams=4, chunk=1 << 20, inflight_per_stream=2, device="cuda", seed=5,
+                 chunk_flop=2e9, age_limit_s=0.25):
         self.device = torch.device(device)
         self.P_max = P_max
-        self.P32 = min(P_max, FP32_MAX_ORDER)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(n_streams)]
         # one handle per stream and dtype: launches that use a handle's global
         # scratch run one after another, so streams with their own handles overlap
         self.hs = {"f64": [sfmm.Handle(P_max, "f64") for _ in self.streams],
-                   "f32": [sfmm.Handle(self.P32, "f32") for _ in self.streams]}
+                   "f32": [sfmm.Handle(P_max, "f32") for _ in self.streams]}
         self.h = {k: v[0] for k, v in self.hs.items()}
         self._sidx = {id(s): i for i, s in enumerate(self.streams)}
-        self.chunk = chunk
+        self.chunk = chunk                   # most translations in one chunk
+        self.chunk_flop = chunk_flop         # target work of one chunk
+        self.age_limit_s = age_limit_s       # ageing bound of admission and dealing
+        nsm = torch.cuda.get_device_properties(self.device).multi_processor_count
+        self.wave = nsm * 8 * 32             # translations of one wave of the batch kernel
         self.inflight = inflight_per_stream
         self.arena = Arena(arena_bytes, self.device)
         self.pool = {}
@@ -144,7 +147,7 @@ class TranslationServer:
     # ----------------------------------------------------------- admission
     def _admit(self, r):
         """Reserve arena space for the request's output, pointers and shifts."""
-        w = 8 if (r.dtype == "f64" or r.p_in > self.P32 or r.p_out > self.P32) else 4
+        w = 8 if r.dtype == "f64" else 4
         S_out = r.p_out * (r.p_out + 1)
         need = [r.count * S_out * w, r.count * 8, r.count * 8, r.count * 3 * w]
         got = []
@@ -185,61 +188,86 @@ class TranslationServer:
             ready.record(stream)
         r.out, r._pin, r._pout, r._sh, r._ready = out, pin, pout, sh, ready
         r._next = 0
-        r.chunks_left = math.ceil(r.count / self.chunk)
+        r.chunks_left = 0                # chunks launched and not yet complete
 
-    def _launch_chunk(self, r, stream, start_ev):
+    def _launch_chunk(self, r, stream):
         a = r._next
-        b = min(r.count, a + self.chunk)
+        b = a + self._chunk_len(r)
         r._next = b
+        r._left -= self._work(r, b - a)
+        r.chunks_left += 1
         h = self.hs["f64" if r._w == 8 else "f32"][self._sidx[id(stream)]]
-        n = b - a
         stream.wait_event(r._ready)
         sfmm.translate_batch(r.op, h, r._pin[a:b], r._pout[a:b], r._sh[a:b], r.p_in, r.p_out,
-                             n, stream=stream)
-        ev = torch.cuda.Event(enable_timing=True)
+                             b - a, stream=stream)
+        ev = torch.cuda.Event()
         ev.record(stream)
         return ev
 
     # ----------------------------------------------------------------- run
+    def _work(self, r, n=None):
+        """FLOP of n translations of the request (all of them by default)."""
+        return translation_flop(r.p_in, r.p_out) * (r.count if n is None else n)
+
+    def _chunk_len(self, r):
+        """Translations in the request's next chunk: about chunk_flop of work,
+        but at least one full wave of the batch kernel (wave translations) so
+        that a chunk alone keeps every SM busy, and at most `chunk`."""
+        per = translation_flop(r.p_in, r.p_out)
+        n = max(self.wave, int(self.chunk_flop // per))
+        return max(1, min(n, self.chunk, r.count - r._next))
+
     def run(self, requests, keep_outputs=False):
         """Serve the requests at their arrival times (seconds after start).
-        Returns the requests with done_ms (device time of completion after the
-        start event) filled in; with keep_outputs the results are copied out of
-        the arena before its space is reused."""
+
+        Admission is first-fit in arrival order: a request whose output does not
+        fit in the arena yet is skipped in favour of later ones that fit, until
+        it has waited `age_limit_s`; from then on nothing is admitted past it.
+        Free stream slots take the next chunk of the admitted request with the
+        least remaining work (shortest remaining work first), except that a
+        request older than `age_limit_s` goes first.  Arrival and completion are
+        both taken on the host clock: done_ms = when the host loop saw the
+        request's last chunk complete, in ms after the start of the run.
+        Returns the finished requests; with keep_outputs the results are copied
+        out of the arena before its space is reused."""
         reqs = sorted(requests, key=lambda r: r.arrival)
-        start = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(self.device)
-        start.record(torch.cuda.current_stream(self.device))
         t0 = time.perf_counter()
-        pending = list(reqs)           # not yet arrived
+        pending = list(reqs)[::-1]     # not yet arrived (pop from the end)
         queue = []                     # arrived, waiting for memory
         active = []                    # admitted, chunks left to launch
         inflight = {i: [] for i in range(len(self.streams))}   # stream -> [(ev, req)]
         finished = []
-        rr = 0
         while pending or queue or active or any(inflight.values()):
             now = time.perf_counter() - t0
-            while pending and pending[0].arrival <= now:
-                queue.append(pending.pop(0))
-            # admission (FIFO)
-            while queue and self._admit(queue[0]):
-                r = queue.pop(0)
-                self._prepare(r, self.streams[r.rid % len(self.streams)])
-                active.append(r)
-            # retire finished chunks
+            while pending and pending[-1].arrival <= now:
+                queue.append(pending.pop())
+            # admission: first fit, bounded by age
+            i = 0
+            while i < len(queue):
+                r = queue[i]
+                if self._admit(r):
+                    queue.pop(i)
+                    self._prepare(r, self.streams[r.rid % len(self.streams)])
+                    r._left = self._work(r)
+                    active.append(r)
+                    continue
+                if now - r.arrival > self.age_limit_s:
+                    break
+                i += 1
+            # retire finished chunks (host clock)
             for si, lst in inflight.items():
                 keep = []
                 for ev, r in lst:
                     if ev.query():
                         r.chunks_left -= 1
-                        if r.chunks_left == 0:
-                            r.done_ms = start.elapsed_time(ev)
+                        if r.chunks_left == 0 and r._next >= r.count:
+                            r.done_ms = 1e3 * (time.perf_counter() - t0)
                             if keep_outputs:
                                 cur = torch.cuda.current_stream(self.device)
                                 cur.wait_event(ev)
                                 # always a copy: the arena space is reused at once
-                                r.out = (r.out.float() if r.out.dtype != torch.float32 else r.out.clone()) \
-                                    if r.dtype == "f32" else r.out.clone()
+                                r.out = r.out.clone()
                                 cur.synchronize()
                             else:
                                 r.out = None
@@ -248,23 +276,25 @@ class TranslationServer:
                     else:
                         keep.append((ev, r))
                 inflight[si] = keep
-            # deal chunks round-robin over the active requests onto free stream slots
+            # deal chunks onto free stream slots
             launched = False
             for si, s in enumerate(self.streams):
                 if len(inflight[si]) >= self.inflight or not active:
                     continue
-                r = active[rr % len(active)]
-                rr += 1
-                ev = self._launch_chunk(r, s, start)
+                now = time.perf_counter() - t0
+                old = [r for r in active if now - r.arrival > self.age_limit_s]
+                r = min(old, key=lambda x: x.arrival) if old else min(active, key=lambda x: (x._left, x.arrival))
+                ev = self._launch_chunk(r, s)
                 inflight[si].append((ev, r))
                 if r._next >= r.count:
                     active.remove(r)
                 launched = True
             if not launched:
-                if pending and not queue and not active and not any(inflight.values()):
-                    time.sleep(max(0.0, min(0.001, pending[0].arrival - (time.perf_counter() - t0))))
-                else:
-                    time.sleep(2e-5)
+                busy = active or queue or any(inflight.values())
+                wait = 5e-5 if busy else 1e-3
+                if pending:
+                    wait = min(wait, max(0.0, pending[-1].arrival - (time.perf_counter() - t0)))
+                time.sleep(wait)
         torch.cuda.synchronize(self.device)
         return finished
 
@@ -311,6 +341,13 @@ def poisson_arrivals(requests, rate_per_s, seed=55):
 
 
 def latency_stats(finished):
+    """Latency percentiles (host clock, arrival to completion), and the
+    percentiles of latency per GFLOP of the request's work (a slowdown
+    measure: the workload's service times span five orders of magnitude)."""
     lat = np.array([r.done_ms - 1e3 * r.arrival for r in finished])
+    work = np.array([translation_flop(r.p_in, r.p_out) * r.count for r in finished]) * 1e-9
+    per = lat / work
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "n": len(lat)}
+            "mean_ms": float(lat.mean()), "n": len(lat),
+            "p50_ms_per_gflop": float(np.percentile(per, 50)),
+            "p99_ms_per_gflop": float(np.percentile(per, 99))}

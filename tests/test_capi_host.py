@@ -52,7 +52,7 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(sf):
     h = ctypes.c_void_p()
     assert sf._lib.sfmm_create(0, 1, ctypes.byref(h)) == 2        # order
     assert sf._lib.sfmm_create(65, 1, ctypes.byref(h)) == 2
-    assert sf._lib.sfmm_create(30, 0, ctypes.byref(h)) == 2       # FP32 limit
+    assert sf._lib.sfmm_create(31, 0, ctypes.byref(h)) == 2       # FP32 limit
     assert sf._lib.sfmm_create(8, 7, ctypes.byref(h)) == 1        # dtype
     assert sf._lib.sfmm_create(8, 1, None) == 1
     assert sf._lib.sfmm_m2l_batch(None, None, None, None, 4, 4, 1, 0, None) == 1

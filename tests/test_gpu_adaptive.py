@@ -29,6 +29,11 @@ def setup():
     h.close()
 
 
+def _radius(tree, node):
+    """Circumradius of an adaptive-tree box (half edge times sqrt(3))."""
+    return float(np.sqrt(3.0) * tree.half[node])
+
+
 def _oracle_M(orc, pts, q, tree, P_node, node):
     sel = tree.order[tree.pt_begin[node]:tree.pt_end[node]]
     return orc.p2m(int(P_node[node]), pts[sel], q[sel], tree.centre[node])
@@ -64,7 +69,8 @@ def test_m2l_waves_fused_and_per_class_agree_with_oracle(setup, orc):
                     want += orc.translate("m2l", int(P_node[s]), Po, Ms, tree.centre[t] - tree.centre[s])
         a, b = ap.off[t], ap.off[t + 1]
         for fused in (True, False):
-            assert U.rel_err(results[fused][a:b], want, Po, "L") <= 1e-12, (t, fused)
+            U.check_rows(results[fused][a:b], want, Po, "L", 1e-12, a=_radius(tree, t),
+                         what=f"target {t} fused={fused}")
 
 
 def test_upward_pass_matches_p2m_of_subtrees(setup, orc):
@@ -78,7 +84,8 @@ def test_upward_pass_matches_p2m_of_subtrees(setup, orc):
     for n in g.choice(inner, size=min(8, len(inner)), replace=False):
         want = _oracle_M(orc, pts, q, tree, P_node, n)
         P = int(P_node[n])
-        assert U.rel_err(M[ap.off[n]:ap.off[n + 1]], want, P, "M") <= 1e-12, n
+        U.check_rows(M[ap.off[n]:ap.off[n + 1]], want, P, "M", 1e-12, a=_radius(tree, n),
+                     what=f"node {n}")
 
 
 def test_autotuner_installs_policies_and_keeps_results(setup, tmp_path):

@@ -55,22 +55,24 @@ def test_grid_m2l_matches_rotation_path_and_oracle(env, orc, ns):
     torch.cuda.synchronize()
     assert h.sync_status() == 0
     a, b = Lg.cpu().numpy(), Lr.cpu().numpy()
-    err = U.rel_err(a, b, P, "L")
-    assert err <= TOL, err
+    rad = U.box_radius(lv.h)
+    # every target against the FP64 rotation path
+    U.check_rows(a, b, P, "L", TOL, a=rad, what=f"grid vs FP64 rotation, side {ns}")
     # accumulate mode adds
     grid.m2l(lv.h, M, Lg, accumulate=True)
     torch.cuda.synchronize()
-    assert U.rel_err(Lg.cpu().numpy(), 2 * b, P, "L") <= TOL
-    # a few targets against the oracle (its own multipoles from the charges)
-    Mh = M.cpu().numpy()
-    for t in g.choice(nb, size=3, replace=False):
-        j0, j1 = lv.m2l_offsets[t], lv.m2l_offsets[t + 1]
-        want = np.zeros(S)
-        for j in range(j0, j1):
-            s = lv.m2l_sources[j]
-            Ms = orc.p2m(P, pos[s], q[s], lv.centres[s])
-            want += orc.translate("m2l", P, P, Ms, lv.m2l_shift[j])
-        assert U.rel_err(a[t], want, P, "L") <= TOL
+    U.check_rows(Lg.cpu().numpy(), 2 * b, P, "L", TOL, a=rad, what="grid accumulate")
+    # 32 targets against the oracle (its own multipoles from the charges)
+    Mh = {}
+    picks = g.choice(nb, size=32, replace=False)
+    want = np.zeros((len(picks), S))
+    for i, t in enumerate(picks):
+        for j in range(lv.m2l_offsets[t], lv.m2l_offsets[t + 1]):
+            s_ = int(lv.m2l_sources[j])
+            if s_ not in Mh:
+                Mh[s_] = orc.p2m(P, pos[s_], q[s_], lv.centres[s_])
+            want[i] += orc.translate("m2l", P, P, Mh[s_], lv.m2l_shift[j])
+    U.check_rows(a[picks], want, P, "L", TOL, a=rad, what="grid vs oracle")
     grid.close()
 
 

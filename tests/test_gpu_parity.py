@@ -1,7 +1,8 @@
 """CUDA path against the oracle, element by element, through the C ABI.
 
-Tolerances: the weighted relative coefficient error (tests/gpu_util.py) must
-be <= 1e-12 in FP64 and <= 1e-5 in FP32 (FP32 at P <= 10)."""
+Tolerances: the weighted relative coefficient error of EVERY expansion
+(tests/gpu_util.py: per output solid, normalised by that solid's own weighted
+norm) must be <= 1e-12 in FP64 and <= 1e-5 in FP32."""
 import numpy as np
 import pytest
 
@@ -38,6 +39,20 @@ def h32(sf):
     h.close()
 
 
+def _charge_expansions(orc, g, count, P, op):
+    """The paper's inputs (config 1 recipe): 32 charges uniform in a unit box
+    at the origin, q ~ U[-1,1]; M by P2M about the origin (M2M, M2L), L by P2L
+    about a centre at distance 3 (L2L); shifts = unit direction x U[2,4]."""
+    pos, q = W.charge_clusters(g, count, 32)
+    sh = W.shifts(g, count, 2.0, 4.0)
+    if op == "l2l":
+        cen = W.unit_directions(g, count) * 3.0
+        C = np.stack([orc.p2l(P, pos[i], q[i], cen[i]) for i in range(count)])
+    else:
+        C = np.stack([orc.p2m(P, pos[i], q[i], np.zeros(3)) for i in range(count)])
+    return C, sh
+
+
 def _config1_inputs(orc, sf, count, P, seed, op):
     """32 charges uniform in a unit box at the origin, q ~ U[-1,1]; multipoles
     by P2M about the origin, locals by P2L about a centre at distance 3.
@@ -72,11 +87,10 @@ def test_config1_p6_4096(sf, orc, h64, op):
     P, count = 6, 4096
     C, Cg, sh = _config1_inputs(orc, sf, count, P, 1, op)
     kind_in = "L" if op == "l2l" else "M"
-    assert U.rel_err(Cg, C, P, kind_in) < 1e-14          # device P2M / P2L
+    U.check_rows(Cg, C, P, kind_in, TOL["f64"], what="device P2M / P2L")
     got = U.run_batch(sf, h64, op, Cg, sh, P, P, "f64")
     want, _ = orc.batch(op, P, P, C, sh)
-    err = U.rel_err(got, want, P, U.out_kind(op))
-    assert err <= TOL["f64"], err
+    U.check_rows(got, want, P, U.out_kind(op), TOL["f64"], what=op)
 
 
 @pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
@@ -89,19 +103,30 @@ def test_mixed_orders(sf, orc, h64, op, p_in, p_out):
     sh = W.shifts(g, count, 2.0, 4.0)
     got = U.run_batch(sf, h64, op, C, sh, p_in, p_out, "f64")
     want, _ = orc.batch(op, p_in, p_out, C, sh)
-    assert U.rel_err(got, want, p_out, U.out_kind(op)) <= TOL["f64"]
+    U.check_rows(got, want, p_out, U.out_kind(op), TOL["f64"], what=f"{op} {p_in}->{p_out}")
 
 
 @pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
 @pytest.mark.parametrize("P", [16, 20, 27, 32])
 def test_high_orders(sf, orc, h64, op, P):
+    """M2M and L2L on random solids; M2L on the expansions of charge
+    clusters.  Random solids with row decay 0.4^n are not the multipole of
+    any charge distribution in the unit box (their weighted top row exceeds
+    the monopole by 1e12 and more): their M2L output is a cancellation of
+    terms ~1e7 larger than itself, so two exact-in-FP64 evaluations (the
+    oracle's naive sum and the rotation path) differ by up to 4e-9 per
+    expansion at P = 32, whereas on charge expansions they agree to ~1e-15."""
     g = W.rng(2000 + P)
     count = 40
-    C = W.random_solids(g, count, P, decay=0.4)
-    sh = W.shifts(g, count, 2.0, 4.0)
+    if op == "m2l":
+        C, sh = _charge_expansions(orc, g, count, P, op)
+    else:
+        C = W.random_solids(g, count, P, decay=0.4)
+        sh = W.shifts(g, count, 2.0, 4.0)
     got = U.run_batch(sf, h64, op, C, sh, P, P, "f64")
     want, _ = orc.batch(op, P, P, C, sh)
-    assert U.rel_err(got, want, P, U.out_kind(op)) <= TOL["f64"]
+    U.check_rows(got, want, P, U.out_kind(op), TOL["f64"], a=U.out_radius(op, sh),
+                 what=f"{op} P={P}")
 
 
 @pytest.mark.parametrize("P", [7, 10])
@@ -112,7 +137,7 @@ def test_ragged_counts(sf, orc, h64, count, P):
     sh = W.shifts(g, count)
     got = U.run_batch(sf, h64, "m2l", C, sh, P, P, "f64")
     want, _ = orc.batch("m2l", P, P, C, sh)
-    assert U.rel_err(got, want, P, "L") <= TOL["f64"]
+    U.check_rows(got, want, P, "L", TOL["f64"], what=f"m2l count={count}")
 
 
 def test_count_zero_is_noop(sf, h64):
@@ -130,7 +155,7 @@ def test_special_shifts(sf, orc, h64, op, P):
     C = W.random_solids(g, len(sh), P)
     got = U.run_batch(sf, h64, op, C, sh, P, P, "f64")
     want, _ = orc.batch(op, P, P, C, sh)
-    assert U.rel_err(got, want, P, U.out_kind(op)) <= TOL["f64"]
+    U.check_rows(got, want, P, U.out_kind(op), TOL["f64"], what=f"{op} special shifts")
 
 
 @pytest.mark.parametrize("op", ["m2m", "l2l"])
@@ -153,7 +178,7 @@ def test_accumulate(sf, orc, h64, op):
     init = W.random_solids(g, 50, P)
     got = U.run_batch(sf, h64, op, C, sh, P, P, "f64", accumulate=True, init=init)
     want, _ = orc.batch(op, P, P, C, sh)
-    assert U.rel_err(got - init, want, P, U.out_kind(op)) <= 1e-11
+    U.check_rows(got, init + want, P, U.out_kind(op), TOL["f64"], what=f"{op} accumulate")
 
 
 def test_result_independent_of_batch(sf, h64):
@@ -168,21 +193,45 @@ def test_result_independent_of_batch(sf, h64):
         assert np.array_equal(one[0], full[i])
 
 
+@pytest.fixture(scope="module")
+def h32_30(sf):
+    h = sf.Handle(30, "f32")
+    yield h
+    h.close()
+
+
 @pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
-@pytest.mark.parametrize("P", [6, 7, 10, 12])
-def test_fp32(sf, orc, h32, op, P):
+@pytest.mark.parametrize("P", [6, 12, 16, 20, 24, 30])
+def test_fp32(sf, orc, h32_30, op, P):
+    """FP32 rotation path at every order of the paper's workloads, each
+    expansion within 1e-5 of the FP64 oracle applied to the same FP32-rounded
+    inputs (P = 6, 12: unrolled kernels; above: generic kernels)."""
     g = W.rng(5000 + P)
-    count = 200
-    C = W.random_solids(g, count, P)
-    sh = W.shifts(g, count)
-    got = U.run_batch(sf, h32, op, C.astype(np.float32), sh.astype(np.float32), P, P, "f32")
-    # the oracle sees exactly the FP32-rounded inputs
-    want, _ = orc.batch(op, P, P, C.astype(np.float32).astype(np.float64),
-                        sh.astype(np.float32).astype(np.float64))
-    assert U.rel_err(got, want, P, U.out_kind(op)) <= TOL["f32"]
+    count = 200 if P <= 20 else 96
+    C, sh = _charge_expansions(orc, g, count, P, op)
+    C32, sh32 = C.astype(np.float32), sh.astype(np.float32)
+    got = U.run_batch(sf, h32_30, op, C32, sh32, P, P, "f32")
+    want, _ = orc.batch(op, P, P, C32.astype(np.float64), sh32.astype(np.float64))
+    U.check_rows(got, want, P, U.out_kind(op), TOL["f32"], a=U.out_radius(op, sh32),
+                 what=f"fp32 {op} P={P}")
+
+
+@pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
+@pytest.mark.parametrize("p_in,p_out", [(30, 27), (24, 30), (7, 18)])
+def test_fp32_mixed_orders(sf, orc, h32_30, op, p_in, p_out):
+    g = W.rng(5100 + p_in + 31 * p_out)
+    C, sh = _charge_expansions(orc, g, 64, p_in, op)
+    C32, sh32 = C.astype(np.float32), sh.astype(np.float32)
+    got = U.run_batch(sf, h32_30, op, C32, sh32, p_in, p_out, "f32")
+    want, _ = orc.batch(op, p_in, p_out, C32.astype(np.float64), sh32.astype(np.float64))
+    U.check_rows(got, want, p_out, U.out_kind(op), TOL["f32"], a=U.out_radius(op, sh32),
+                 what=f"fp32 {op} {p_in}->{p_out}")
 
 
 def _run_lists(sf, orc, h, op, P_in, P_out, accumulate, seed, dtype="f64", maxlen=40, nt=70):
+    """Target-major lists of lengths 0..maxlen; FP64 runs use random solids,
+    FP32 runs the paper's inputs (expansions of charge clusters, the form whose
+    FP32 rounding the 1e-5 tolerance is stated for)."""
     import torch
     g = W.rng(seed)
     lens = g.integers(0, maxlen + 1, size=nt)
@@ -191,7 +240,10 @@ def _run_lists(sf, orc, h, op, P_in, P_out, accumulate, seed, dtype="f64", maxle
     np.cumsum(lens, out=offs[1:])
     nnz = int(offs[-1])
     nsrc = 90
-    S = W.random_solids(g, nsrc, P_in)
+    if dtype == "f32":
+        S, _ = _charge_expansions(orc, g, nsrc, P_in, op)
+    else:
+        S = W.random_solids(g, nsrc, P_in)
     src_idx = g.integers(0, nsrc, size=nnz)
     sh = W.shifts(g, nnz)
     init = W.random_solids(g, nt, P_out)
@@ -214,7 +266,7 @@ def _run_lists(sf, orc, h, op, P_in, P_out, accumulate, seed, dtype="f64", maxle
     for t in range(nt):
         for j in range(offs[t], offs[t + 1]):
             want[t] += each[j]
-    return U.rel_err(got, want, P_out, U.out_kind(op))
+    return U.rel_err_rows(got, want, P_out, U.out_kind(op))
 
 
 @pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
@@ -224,14 +276,14 @@ def test_lists_fixed_orders(sf, orc, h64, op, accumulate, P):
     """Lists at the orders with fully unrolled kernels (groups of 8 or 32 lanes
     per target, lengths 0..70 so that targets take several rounds)."""
     err = _run_lists(sf, orc, h64, op, P, P, accumulate, 6100 + P, maxlen=70)
-    assert err <= TOL["f64"], err
+    assert err.max() <= TOL["f64"], (int(err.argmax()), err.max())
 
 
 @pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
 @pytest.mark.parametrize("P", [6, 8, 10, 12])
 def test_lists_fixed_orders_fp32(sf, orc, h32, op, P):
     err = _run_lists(sf, orc, h32, op, P, P, False, 6200 + P, dtype="f32")
-    assert err <= TOL["f32"], err
+    assert err.max() <= TOL["f32"], (int(err.argmax()), err.max())
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -250,7 +302,10 @@ def test_lists_m2l_special_shifts(sf, orc, h64, h32, dtype, P):
         base[2, 0] = 1e-30                          # representable in FP32
     g = W.rng(6300 + P)
     nt, per = 40, len(base)
-    S = W.random_solids(g, nt * per, P)
+    if dtype == "f32":
+        S, _ = _charge_expansions(orc, g, nt * per, P, "m2l")
+    else:
+        S = W.random_solids(g, nt * per, P)
     sh = np.tile(base, (nt, 1))
     if dtype == "f32":
         S, sh = (a.astype(np.float32).astype(np.float64) for a in (S, sh))
@@ -266,8 +321,7 @@ def test_lists_m2l_special_shifts(sf, orc, h64, h32, dtype, P):
     got = dO.double().cpu().numpy()
     each, _ = orc.batch("m2l", P, P, S, sh)
     want = each.reshape(nt, per, -1).sum(axis=1)
-    err = U.rel_err(got, want, P, U.out_kind("m2l"))
-    assert err <= TOL[dtype], err
+    U.check_rows(got, want, P, "L", TOL[dtype], what=f"{dtype} lists special shifts")
 
 
 @pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
@@ -304,7 +358,7 @@ def test_lists(sf, orc, h64, op, accumulate):
     for t in range(nt):
         for j in range(offs[t], offs[t + 1]):
             want[t] += each[j]
-    assert U.rel_err(got, want, P_out, U.out_kind(op)) <= TOL["f64"]
+    U.check_rows(got, want, P_out, U.out_kind(op), TOL["f64"], what=f"{op} lists")
 
 
 @pytest.mark.parametrize("P", [4, 6])
@@ -383,7 +437,7 @@ def test_lists_multi_lanes_per_target(sf, orc, h64, lanes):
             if lens[t] == 0:
                 assert not got[t].any(), t          # an empty list gives zeros
             else:
-                assert U.rel_err(got[t, :po * (po + 1)], w, po, U.out_kind(op)) <= TOL["f64"], (op, t)
+                U.check_rows(got[t, :po * (po + 1)], w, po, U.out_kind(op), TOL["f64"], what=f"{op} target {t}")
             t += 1
 
 
