@@ -251,22 +251,35 @@ sfmm_status sfmm_reserve_scratch(sfmm_handle h, int p_in_max);
  * sfmm_grid_m2l: L (+)= M2L of every box's interaction list on an nside^3 grid
  * (nside a multiple of 8, box i at (ix*nside + iy)*nside + iz, solids of order
  * 16 stored contiguously, FP64 device arrays M and L).  Operands are split
- * into three BF16 parts (hi + mid + lo, about 24 bits) and multiplied as six
- * BF16 products with FP32 accumulation over 2 offsets and FP64 accumulation
- * per target; results agree with the FP64 rotation path to about 3e-6, every
- * target within 1e-5 (weighted coefficient error).  Asynchronous on
- * `stream`; one call at a time per grid object.  A device-side wait that gives
- * up sets bit 4 of the handle's status word (sfmm_sync_status); bit 8 means
- * that, after such a time-out, copies or MMAs already issued did not finish
- * within 2 s either (the kernel then keeps its tensor memory allocated).
+ * into two FP16 parts (hi + lo, 22 significant bits; operator rows and the
+ * call's sources each scaled by a power of two into the FP16 range, undone
+ * exactly on output) and multiplied as three products with FP32 accumulation
+ * over 2 offsets, then added into float-float sums per target (about 48
+ * bits) and written once in FP64: every target within 1e-5 (weighted
+ * coefficient error) of the FP64 rotation path, and the same result on every
+ * run.  Asynchronous on `stream`; one call at a time per grid object.  A
+ * device-side wait that gives up sets bit 4 of the handle's status word
+ * (sfmm_sync_status); bit 8 means that, after such a time-out, copies or MMAs
+ * already issued did not finish within 2 s either (the kernel then keeps its
+ * tensor memory allocated); bit 16 means the kernel found its shared memory
+ * misaligned for its 128-byte swizzled tiles and did nothing.
  * Errors: SFMM_ERR_ARG, SFMM_ERR_ORDER (handle not FP64 or P_max < 16),
  * SFMM_ERR_UNSUPPORTED (P != 16), SFMM_ERR_NOMEM, SFMM_ERR_CUDA.
+ * sfmm_grid_inject_timeout: fault injection for tests of the time-out path.
+ * With after_chunks > 0, the copy thread of every CTA of the following calls
+ * acts as if its wait for a free pipeline stage had timed out once it has
+ * issued that many operand chunks: the kernel then takes its time-out path
+ * (status bit 4, the MMA and epilogue roles give up, bounded drain of the
+ * copies and MMAs in flight, tensor memory freed) and the call's result is
+ * undefined.  after_chunks = 0 turns the injection off.  No GPU fault is
+ * involved: the injected time-out is the host's request.  Errors: SFMM_ERR_ARG.
  */
 typedef struct sfmm_grid_ctx *sfmm_grid;
 sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out);
 sfmm_status sfmm_grid_m2l(sfmm_grid g, double box_size, const void *M, void *L, int accumulate,
                           sfmm_stream stream);
 sfmm_status sfmm_grid_destroy(sfmm_grid g);
+sfmm_status sfmm_grid_inject_timeout(sfmm_grid g, long long after_chunks);
 
 /*
  * Particle-to-expansion helpers (not part of the paper's translation library;

@@ -11,26 +11,39 @@
 // T_u x over its 189 offsets.  Targets of the same child octant share the same
 // 189 offsets, so a tile of 128 same-octant targets (64 when the grid side is
 // not a multiple of 16) is one GEMM with K = 189 * 256 on the 5th-generation
-// tensor cores:
-//   * T_u and x are split into three BF16 parts, hi + mid + lo (about 24
-//     significant bits), and multiplied as the six products hi*hi, hi*mid,
-//     mid*hi, hi*lo, lo*hi, mid*mid (tcgen05.mma kind::f16) with FP32
-//     accumulation in tensor memory (two 128-row halves x 128 columns, two
-//     buffers);
-//   * every 2 offsets the accumulator is read out (tcgen05.ld) and added into
-//     the target's FP64 sum in global memory (FP32 rounding over longer runs
-//     of offsets pushed single targets above a 1e-5 relative error);
-//   * operand chunks (16 of K) are staged in shared memory in five stages: the
-//     T_u chunk, stored pre-tiled, by one bulk copy; the targets' source
-//     vectors, stored split by coordinate parity, by three 5-D tensor copies;
+// tensor cores (tcgen05.mma kind::f16, M = 128, N = tile, K = 16):
+//   * operands are split into two FP16 parts, hi + lo (22 significant bits),
+//     multiplied as the three products hi*hi, hi*lo, lo*hi with FP32
+//     accumulation in tensor memory (the dropped lo*lo is 2^-22 relative).
+//     FP16 has 5 exponent bits, so every operator row n is scaled by a power of
+//     two that brings its largest entry near 2^12 (fixed when the grid is
+//     created), and all sources of a call by one power of two that brings
+//     their largest magnitude below 2^14 (found on the device per call); the
+//     output undoes both exactly;
+//   * every 2 offsets the FP32 accumulator is added into a float-float sum
+//     (hi + lo, Knuth's two-sum) kept in tensor memory, so a target's sum over
+//     the 189 offsets carries about 48 bits; at the end of its work unit the
+//     CTA writes the sum once, in FP64, to its own slot: no atomics, and a
+//     target's result is the same on every run;
+//   * work units are (tile, operator row half, K half): the CTA computes rows
+//     [128 h, 128 h + 128) of T_u x for the offsets of its K half, and the
+//     unpack kernel adds the two K halves in a fixed order;
+//   * operand chunks (64 of K, four MMAs) are staged in shared memory in three
+//     stages of 64 KB: the T_u chunk of the row half (both parts), stored
+//     pre-tiled, by one bulk copy; the targets' source vectors (both parts),
+//     stored split by coordinate parity, by two 5-D tensor copies with 128-byte
+//     rows (rows of 32 bytes, 16 of K, held the tensor copies to a quarter of
+//     the rate the MMAs need);
 //   * one thread issues copies, one issues MMAs, four warps drain the
-//     accumulators; one persistent CTA per SM.
+//     accumulators (the float-float update of one 2-offset group overlaps the
+//     MMAs of the next, two accumulator buffers); one persistent CTA per SM.
 // T_u are built once per grid object with the FP64 rotation-based M2L on the
 // 256 basis vectors of every offset.  Every mbarrier wait is bounded: on
 // time-out the kernel records SFMM_GRID_TIMEOUT in the status word, stops
-// issuing work, frees its tensor memory and returns.
+// issuing work, waits (bounded by time only) for its copies and MMAs in
+// flight, frees its tensor memory and returns.
 #include <cuda.h>
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -49,17 +62,22 @@ namespace {
 
 constexpr int GP = 16;             // order of the grid operators
 constexpr int KD = GP * GP;        // 256 reals per box in the reduced layout
-constexpr int KC = 16;             // K chunk staged in shared memory (one BF16 MMA)
-constexpr int NST = 5;             // pipeline stages
+constexpr int KC = 64;             // K chunk staged in shared memory (four FP16 MMAs of K = 16)
+constexpr int UK = 16;             // K of one tcgen05.mma kind::f16
 constexpr int NKC = KD / KC;       // chunks per offset
-constexpr int NPART = 3;           // operand parts: hi, mid, lo (BF16 each)
-constexpr int A_PART = KD * KC * 2;   // one part of an A chunk: 256 rows x 16 K x 2 B = 8 KB
-constexpr int FLUSH = 2;           // offsets accumulated in FP32 before an FP64 flush
+constexpr int NPART = 2;           // operand parts: hi, lo (FP16 each)
+constexpr int HROWS = 128;         // operator rows of one CTA (one half of KD)
+constexpr int A_PART = HROWS * KC * 2;   // one part of an A chunk: 128 rows x 64 K x 2 B = 16 KB
+constexpr int A_CHUNK = NPART * A_PART;  // A chunk of one row half, both parts: 32 KB
+constexpr int FLUSH = 2;           // offsets accumulated in FP32 before the float-float update
 constexpr int NU = 189;            // offsets of a child octant
-constexpr int NCH_ALL = NU * NKC;  // K chunks of a tile
+constexpr int KS = 2;              // K halves: offsets [0, 95) and [95, 189)
 constexpr int NCODE = 343;         // offset codes ((dx+3)*7 + dy+3)*7 + dz+3
+constexpr int OP_ROW_EXP = 12;     // operator rows scaled to a largest entry in [2^11, 2^12)
+constexpr int SRC_EXP = 14;        // sources scaled to a largest magnitude below 2^14
 constexpr int STATUS_GRID_TIMEOUT = 4;       // a pipeline wait gave up
 constexpr int STATUS_GRID_DRAIN = 8;         // work in flight did not finish within 2 s
+constexpr int STATUS_GRID_ALIGN = 16;        // shared memory not 1024-byte aligned (nothing ran)
 
 // reduced real layout of a solid of order GP: row n at n^2: Re m=0..n, Im m=1..n
 __host__ __device__ inline void reduced_index(int e, int *n, int *m, bool *im) {
@@ -71,14 +89,18 @@ __host__ __device__ inline void reduced_index(int e, int *n, int *m, bool *im) {
     *m = *im ? q - nn : q;
 }
 
+// first offset of K half ks (KS halves of the NU offsets)
+__host__ __device__ inline int k_begin(int ks) { return (ks * NU + KS - 1) / KS; }
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
 // shared-memory matrix descriptor of a K-major operand.  layout 0: no swizzle,
 // core matrices of 8 rows x 16 bytes, lbo = byte step between core matrices
-// along K, sbo = along M/N.  layout 4: 64-byte swizzle, rows of 64 bytes,
-// sbo = step between groups of 8 rows (lbo unused).
+// along K, sbo = along M/N.  layout 2: 128-byte swizzle, rows of 128 bytes,
+// sbo = step between groups of 8 rows; the K = 16 steps inside a row start
+// 32 bytes apart.
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFF);
@@ -89,40 +111,22 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
     return d;
 }
 
-// byte offset of (row r, k) inside a [rows x KC] BF16 K-major tile of core
+// byte offset of (row r, k) inside a [rows x KC] FP16 K-major tile of core
 // matrices of 8 rows x 8 K (16 bytes per row)
-__device__ __forceinline__ int koff(int r, int k) {
+__host__ __device__ __forceinline__ int koff(int r, int k) {
     return ((r >> 3) * (KC / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-// v = hi + mid + lo in BF16 (8 significant bits each): the three parts carry
-// about 24 bits of v, the products dropped below (mid*lo, lo*mid, lo*lo) are
-// of relative size 2^-24
-__device__ __forceinline__ void split3(double v, unsigned short *hi, unsigned short *mid,
-                                       unsigned short *lo) {
-    // (FP64 arithmetic: used once per operator entry when a grid is created)
-    const __nv_bfloat16 h = __double2bfloat16(v);
-    const double r1 = v - (double)__bfloat162float(h);
-    const __nv_bfloat16 m = __double2bfloat16(r1);
-    const double r2 = r1 - (double)__bfloat162float(m);
-    const __nv_bfloat16 l = __double2bfloat16(r2);
-    *hi = __bfloat16_as_ushort(h);
-    *mid = __bfloat16_as_ushort(m);
-    *lo = __bfloat16_as_ushort(l);
+// v = hi + lo in FP16 (11 significant bits each, 22 together)
+__device__ __forceinline__ void split2(double v, __half *hi, __half *lo) {
+    const __half h = __double2half(v);
+    *hi = h;
+    *lo = __double2half(v - (double)__half2float(h));
 }
-
-// the same split of an FP32 value in FP32 arithmetic (the subtractions are
-// exact): the per-call packing of the sources, where FP64 work would cost more
-// than the copy itself on this GPU's FP64 pipe
-__device__ __forceinline__ void split3f(float v, unsigned short *hi, unsigned short *mid,
-                                        unsigned short *lo) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const float r1 = v - __bfloat162float(h);
-    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(m);
-    *hi = __bfloat16_as_ushort(h);
-    *mid = __bfloat16_as_ushort(m);
-    *lo = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
+__device__ __forceinline__ void split2f(float v, __half *hi, __half *lo) {
+    const __half h = __float2half_rn(v);
+    *hi = h;
+    *lo = __float2half_rn(v - __half2float(h));
 }
 
 // ----------------------------------------------------------------- kernels
@@ -132,61 +136,130 @@ struct Scales {
     double s[GP * (GP + 1) / 2];
 };
 
-// x = M c / h^{k+1} in the reduced layout on the halo grid, split into BF16 hi, mid, lo.
-// The halo grid (side nh = nside + 6, even) is stored split by coordinate
-// parity, [px py pz][hx/2][hy/2][hz/2][KD], so that the sources of a tile of
-// same-parity targets under one offset form one dense box.
-__global__ void pack_kernel(const double *M, int nside, Scales sc, unsigned short *xhi,
-                            unsigned short *xmid, unsigned short *xlo) {
-    const int nh = nside + 6, nh2 = nh / 2;
-    const long long total = (long long)nh * nh * nh * KD;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long b = i / KD;
-        const int e = (int)(i % KD);
-        const int hz2 = (int)(b % nh2), hy2 = (int)((b / nh2) % nh2), hx2 = (int)((b / nh2 / nh2) % nh2);
-        const int par = (int)(b / ((long long)nh2 * nh2 * nh2));
+// index tables of the two layouts (filled by sfmm_grid_create):
+//   reduced index e (row n at n^2: Re m = 0..n, Im m = 1..n) -> position in a
+//   solid and scale index n(n+1)/2 + m;  solid position p -> reduced index
+//   (-1 for Im C_n^0, which the reduced layout drops) and scale index
+constexpr int SOLID = GP * (GP + 1);
+__constant__ short c_pos_of_e[KD];
+__constant__ unsigned char c_sidx_of_e[KD];
+__constant__ short c_e_of_pos[SOLID];
+__constant__ unsigned char c_sidx_of_pos[SOLID];
+
+// The three kernels below give every thread one fixed coefficient (its
+// table entries and scale factor are read once: lanes reading different
+// entries of constant or parameter memory would be serialised) and let the
+// blocks stride over boxes.
+constexpr int SOLID_THREADS = 288;             // SOLID rounded up to whole warps
+
+// largest |x| of the level's sources (float bits of a non-negative float
+// order like unsigned integers), one atomicMax per block
+__global__ void __launch_bounds__(SOLID_THREADS) xmax_kernel(const double *M, long long nboxes, Scales sc,
+                                                             unsigned int *xmax) {
+    const int p = threadIdx.x;
+    float v = 0.f;
+    if (p < SOLID) {
+        const double f = sc.s[c_sidx_of_pos[p]];
+        for (long long b = blockIdx.x; b < nboxes; b += gridDim.x)
+            v = fmaxf(v, fabsf((float)(M[b * SOLID + p] * f)));
+    }
+    for (int d = 16; d > 0; d >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, d));
+    __shared__ float wmax[SOLID_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = 0.f;
+        for (int w = 0; w < SOLID_THREADS / 32; ++w) b = fmaxf(b, wmax[w]);
+        atomicMax(xmax, __float_as_uint(b));
+    }
+}
+
+// exponent g of the sources' scale 2^g: largest |x| * 2^g < 2^SRC_EXP
+__device__ __forceinline__ int source_exp(const unsigned int *xmax) {
+    const float m = __uint_as_float(*xmax);
+    if (!(m > 0.f)) return 0;
+    int e;
+    frexpf(m, &e);                       // m < 2^e
+    return SRC_EXP - e;
+}
+
+// x = M c / h^{k+1} 2^g in the reduced layout on the halo grid, split into FP16
+// hi and lo.  The halo grid (side nh = nside + 6, even) is stored split by
+// coordinate parity, [px py pz][hx/2][hy/2][hz/2][KD], so that the sources of
+// a tile of same-parity targets under one offset form one dense box.  Thread
+// e of a block writes coefficient e of the halo boxes the block strides over.
+__global__ void __launch_bounds__(KD) pack_kernel(const double *M, int nside, Scales sc,
+                                                  const unsigned int *xmax, __half *xhi, __half *xlo) {
+    const int nh2 = (nside + 6) / 2, nbox = 8 * nh2 * nh2 * nh2;
+    const int e = threadIdx.x;
+    const int pos = c_pos_of_e[e];
+    const double f = sc.s[c_sidx_of_e[e]];
+    const float g = ldexpf(1.f, source_exp(xmax));
+    for (int blk = blockIdx.x; blk < nbox; blk += gridDim.x) {
+        const int hz2 = blk % nh2, hy2 = (blk / nh2) % nh2, hx2 = (blk / (nh2 * nh2)) % nh2;
+        const int par = blk / (nh2 * nh2 * nh2);
         const int hx = 2 * hx2 + ((par >> 2) & 1) - 3, hy = 2 * hy2 + ((par >> 1) & 1) - 3,
                   hz = 2 * hz2 + (par & 1) - 3;
         float v = 0.f;
         if (hx >= 0 && hx < nside && hy >= 0 && hy < nside && hz >= 0 && hz < nside) {
-            int n, m;
-            bool im;
-            reduced_index(e, &n, &m, &im);
             const long long box_id = ((long long)hx * nside + hy) * nside + hz;
-            const double *s = M + box_id * (GP * (GP + 1));
-            const double val = s[n * (n + 1) + (im ? n + 1 + m : m)];
-            v = (float)(val * sc.s[n * (n + 1) / 2 + m]);
+            v = (float)(M[box_id * SOLID + pos] * f) * g;      // the power of two is exact
         }
-        split3f(v, xhi + i, xmid + i, xlo + i);
+        const long long i = (long long)blk * KD + e;
+        split2f(v, xhi + i, xlo + i);
     }
 }
 
-// L (+)= y c / h^n from the reduced layout (FP64 accumulator y).
-__global__ void unpack_kernel(const double *y, int nside, Scales sc, double *L, int accumulate) {
-    const long long total = (long long)nside * nside * nside * (GP * (GP + 1));
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long b = i / (GP * (GP + 1));
-        const int p = (int)(i % (GP * (GP + 1)));
-        int n = 0;
-        while ((n + 1) * (n + 2) <= p) ++n;
-        const int q = p - n * (n + 1);
-        const bool im = q > n;
-        const int m = im ? q - n - 1 : q;
+// L (+)= (sum over the K halves, in order) y 2^{-row_exp - g} c / h^n from the
+// reduced layout; thread p of a block writes coefficient p of its boxes.
+__global__ void __launch_bounds__(SOLID_THREADS) unpack_kernel(const double *ypart, int nside, Scales sc,
+                                                               const int *row_exp, const unsigned int *xmax,
+                                                               double *L, int accumulate) {
+    const long long nb = (long long)nside * nside * nside;
+    const int p = threadIdx.x;
+    if (p >= SOLID) return;
+    const int e = c_e_of_pos[p];
+    const double f = e >= 0 ? ldexp(sc.s[c_sidx_of_pos[p]], -row_exp[e] - source_exp(xmax)) : 0.0;
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
         double v = 0.0;
-        if (!(im && m == 0)) {
-            const int e = n * n + (im ? n + m : m);
-            v = y[b * KD + e] * sc.s[n * (n + 1) / 2 + m];
+        if (e >= 0) {
+            double y = 0.0;
+            for (int ks = 0; ks < KS; ++ks) y += ypart[((long long)ks * nb + b) * KD + e];
+            v = y * f;
         }
-        L[i] = accumulate ? L[i] + v : v;
+        double *dst = L + b * SOLID + p;
+        *dst = accumulate ? *dst + v : v;
+    }
+}
+
+// largest |T_u[e'][j]| over every offset and column, one block per operator row e'
+__global__ void operator_rowmax_kernel(const double *L, int ncodes, const double *c, double *rowmax) {
+    const int ep = blockIdx.x;
+    int n, m;
+    bool im;
+    reduced_index(ep, &n, &m, &im);
+    const int pos = n * (n + 1) + (im ? n + 1 + m : m);
+    const double ic = 1.0 / c[n * (n + 1) / 2 + m];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < ncodes * KD; i += blockDim.x)
+        v = fmax(v, fabs(L[(long long)i * (GP * (GP + 1)) + pos] * ic));
+    for (int d = 16; d > 0; d >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, d));
+    __shared__ double wmax[32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmax(b, wmax[w]);
+        rowmax[ep] = b;
     }
 }
 
 // operators: T[code][e'][j] from the FP64 M2L of basis vector j (raw solid of
-// order GP), converted to y = L / c in the reduced layout and split hi/mid/lo.
+// order GP), converted to y = L / c in the reduced layout, scaled by
+// 2^row_exp[e'] and split hi/lo; stored pre-tiled as
+// [code][chunk][row half][hi | lo][K-major core-matrix tile of 128 rows x KC]
 __global__ void operator_kernel(const double *L, const int *codes, int ncodes, const double *c,
-                                unsigned short *top) {
+                                const int *row_exp, __half *top) {
     const long long total = (long long)ncodes * KD * KD;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -197,21 +270,22 @@ __global__ void operator_kernel(const double *L, const int *codes, int ncodes, c
         bool im;
         reduced_index(ep, &n, &m, &im);
         const double *s = L + ((long long)k * KD + j) * (GP * (GP + 1));
-        const double v = s[n * (n + 1) + (im ? n + 1 + m : m)] / c[n * (n + 1) / 2 + m];
-        // pre-tiled: [code][chunk][hi|mid|lo][K-major core-matrix tile of 256 rows x KC]
-        const int ch = j / KC, kk = j % KC;
+        const double v = ldexp(s[n * (n + 1) + (im ? n + 1 + m : m)] / c[n * (n + 1) / 2 + m], row_exp[ep]);
+        const int ch = j / KC, kk = j % KC, hh = ep / HROWS, r = ep % HROWS;
         unsigned char *base = reinterpret_cast<unsigned char *>(top) +
-                              ((long long)codes[k] * NKC + ch) * NPART * A_PART + koff(ep, kk);
-        split3(v, reinterpret_cast<unsigned short *>(base), reinterpret_cast<unsigned short *>(base + A_PART),
-               reinterpret_cast<unsigned short *>(base + 2 * A_PART));
+                              (((long long)codes[k] * NKC + ch) * 2 + hh) * A_CHUNK + koff(r, kk);
+        split2(v, reinterpret_cast<__half *>(base), reinterpret_cast<__half *>(base + A_PART));
     }
 }
 
 struct GemmArgs {
-    const unsigned short *top;  // pre-tiled operators, [NCODE][NKC][hi|mid|lo][A_PART bytes]
-    double *y;                  // [ns^3][KD], FP64 sums, zeroed before the launch
+    const __half *top;          // pre-tiled operators, [NCODE][NKC][2][hi|lo][A_PART bytes]
+    double *ypart;              // [KS][ns^3][KD], FP64 sums of the two K halves
     int nside;
     int *status;
+    long long inject_after;     // > 0: the copy thread acts as if its wait for a free
+                                // stage timed out once it has issued this many chunks
+                                // (fault injection for tests of the time-out path)
 };
 
 __device__ __forceinline__ bool try_wait(uint32_t bar, uint32_t parity) {
@@ -253,35 +327,60 @@ __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity) {
     return false;
 }
 
-// Work units: (K slab, tile) pairs in slab-major order, a slab being the K
-// chunks of GW consecutive chunks (FLUSH offsets) of a tile; one unit is one
-// FP32 accumulation group.  CTA c takes units c, c + G, c + 2G, ... so that at
-// any time all CTAs work on the same one or two slabs: the operator chunks and
-// source slices in use at once stay few and are served from L2.
+// 32 consecutive tensor-memory columns of the warp's 32 lanes: thread = lane
+__device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t *v) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+                   "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                   "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(ta));
+}
+__device__ __forceinline__ void tmem_st32(uint32_t ta, const uint32_t *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+                 "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                 "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+                 :: "r"(ta), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+                    "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]),
+                    "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]),
+                    "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+                 : "memory");
+}
+
+// Work units: (tile, operator row half, K half), ordered K half, row half,
+// octant, tile, and dealt round-robin to the persistent CTAs, so that the CTAs
+// of one round run the same offset sequence on neighbouring tiles at the same
+// time and the operator chunks in use stay few and are served from L2.  A unit
+// walks the K chunks of its offsets in groups of GW chunks (FLUSH offsets),
+// one FP32 accumulation each.
 constexpr int GW = NKC * FLUSH;
-constexpr int NSLAB = (NCH_ALL + GW - 1) / GW;
 
-// dynamic shared memory: NST stages of A (hi, mid, lo) and B (hi, mid, lo), then
-// 8 KB for the mbarriers, the TMEM slot, the abort flag and the offset codes of
-// the 8 octants
+// pipeline stages: 3 of 64 KB for 128-target tiles, 4 of 48 KB for 64-target tiles
 template <int NT>
-constexpr int smem_gemm() { return NST * (NPART * A_PART + NPART * NT * KC * 2) + 8192; }
+constexpr int n_stages() { return NT == 128 ? 3 : 4; }
 
-// Persistent, warp-specialised GEMM over (K slab, tile) units dealt round-robin.
+// dynamic shared memory: the stages of A (hi, lo) and B (hi, lo), then 8 KB for
+// the mbarriers, the TMEM slot, the abort flags and the offset codes of the 8 octants
+template <int NT>
+constexpr int smem_gemm() { return n_stages<NT>() * (A_CHUNK + NPART * NT * KC * 2) + 8192; }
+
+// Persistent, warp-specialised GEMM over the work units.
 //   warp 4, one thread: copies.  For chunk i it waits until the MMAs of chunk
 //     i - NST have freed the stage (`empty`), sets the stage's `full` mbarrier
 //     to expect the chunk's bytes and issues one bulk copy of the pre-tiled
-//     T_u chunk (A, hi, mid and lo) and three 5-D tensor copies of the
-//     targets' source vectors (B, hi, mid and lo, 32-byte swizzled rows).
+//     T_u chunk of the unit's row half (hi and lo) and two 5-D tensor copies of
+//     the targets' source vectors (hi and lo, 128-byte swizzled rows).
 //   warp 5, one thread: MMA issue.  For chunk i it waits on `full`, issues the
-//     chunk's tcgen05.mma into one of two accumulator buffers and commits them
-//     to the stage's `empty` mbarrier; the last chunk of a unit is also
+//     chunk's twelve tcgen05.mma into one of two accumulator buffers and commits
+//     them to the stage's `empty` mbarrier; the last chunk of a group is also
 //     committed to `acc_full` of its buffer.
-//   warps 0-3: epilogue.  For every unit they wait on `acc_full`, read their 32
-//     TMEM lanes (rows) of the buffer, add the FP32 partial sums into the FP64
-//     target sums with atomic adds (the slabs of a tile are spread over CTAs),
-//     and arrive on `acc_empty`, which the MMA thread waits on before it reuses
-//     the buffer.  The epilogue of one unit overlaps the MMAs of the next.
+//   warps 0-3: epilogue.  For every group they wait on `acc_full`, read their
+//     32 TMEM lanes (operator rows) of the buffer and add it into the unit's
+//     float-float sums (two more TMEM column ranges), then arrive on
+//     `acc_empty`, which the MMA thread waits on before it reuses the buffer.
+//     After a unit's last group they write its sums once, in FP64.
 // Every wait is bounded; a time-out sets the abort flag and the status word,
 // the other roles give up their waits, the copy and MMA threads wait for their
 // work in flight (bounded by time only, whatever the abort flag says), and the
@@ -289,13 +388,15 @@ constexpr int smem_gemm() { return NST * (NPART * A_PART + NPART * NT * KC * 2) 
 // of the status word is set and the tensor memory is kept.
 template <int NT>
 __global__ void __launch_bounds__(192, 1)
-grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_mid,
-                 const __grid_constant__ CUtensorMap tm_lo) {
+grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    constexpr int B_PART = NT * KC * 2;             // 4 or 2 KB
-    constexpr int STAGE = NPART * A_PART + NPART * B_PART;
+    constexpr int NST = n_stages<NT>();
+    constexpr int B_PART = NT * KC * 2;             // 16 or 8 KB
+    constexpr int STAGE = A_CHUNK + NPART * B_PART;
     constexpr int TZ = NT / 16;                     // tile depth along z
-    constexpr uint32_t TCOLS = 4 * NT;              // 2 buffers x 2 row halves x NT columns
+    // tensor memory: [0, 2 NT) FP32 accumulators (two buffers), [2 NT, 3 NT)
+    // float-float high parts, [3 NT, 4 NT) low parts
+    constexpr uint32_t TCOLS = 4 * NT;
     uint64_t *full = reinterpret_cast<uint64_t *>(sm + NST * STAGE);
     uint64_t *empty = full + NST;
     uint64_t *acc_full = empty + NST;
@@ -308,8 +409,14 @@ grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __
     const int ns = a.nside, half_ns = ns / 2, tpd = half_ns / 4, tpz = half_ns / TZ;
     const int tiles = tpd * tpd * tpz;
     const int n_tiles = 8 * tiles;
-    const int n_units = NSLAB * n_tiles;
+    const int n_units = KS * 2 * n_tiles;
     const int G = gridDim.x;
+    const long long nb = (long long)ns * ns * ns;
+    // the 128-byte swizzled tiles need 1024-byte aligned stages
+    if (smem_u32(sm) & 1023u) {
+        if (tid == 0) atomicOr(a.status, STATUS_GRID_ALIGN);
+        return;
+    }
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(tslot)), "r"(TCOLS));
@@ -360,41 +467,41 @@ grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __
             for (int s = 0; s < NST; ++s) last[s] = -1;
             bool ok = true;
             for (int u = blockIdx.x; u < n_units && ok; u += G) {
-                const int tile_g = u % n_tiles, c_begin = (u / n_tiles) * GW;
-                const int c_end = (c_begin + GW < NCH_ALL) ? c_begin + GW : NCH_ALL;
+                const int tile_g = u % n_tiles, hh = (u / n_tiles) & 1, ks = u / (2 * n_tiles);
+                const int c_begin = k_begin(ks) * NKC, c_end = k_begin(ks + 1) * NKC;
                 const int cls = tile_g / tiles, tile = tile_g % tiles;
                 const int bx = (cls >> 2) & 1, by = (cls >> 1) & 1, bz = cls & 1;
                 const int tx = tile / (tpd * tpz), ty = (tile / tpz) % tpd, tz = tile % tpz;
-                int c1 = 0, c2 = 0, c3 = 0, c4 = 0;
-                const unsigned char *abase = nullptr;
+                int c1 = 0, c2 = 0, c3 = 0, c4 = 0, code = 0;
                 for (int ci = c_begin; ci < c_end; ++ci, ++i) {
                     if (ci == c_begin || ci % NKC == 0) {
-                        const int code = codes[cls * NU + ci / NKC];
+                        code = codes[cls * NU + ci / NKC];
                         const int sx = bx - (code / 49 - 3) + 3, sy = by - ((code / 7) % 7 - 3) + 3,
                                   sz = bz - (code % 7 - 3) + 3;
                         c1 = tz * TZ + (sz >> 1);
                         c2 = ty * 4 + (sy >> 1);
                         c3 = tx * 4 + (sx >> 1);
                         c4 = ((sx & 1) << 2) | ((sy & 1) << 1) | (sz & 1);
-                        abase = reinterpret_cast<const unsigned char *>(a.top) + (long long)code * NKC * NPART * A_PART;
                     }
                     const int stg = (int)(i % NST), kc = (ci % NKC) * KC;
-                    if (i >= NST && !wait_or_abort(smem_u32(empty + stg), (uint32_t)(((i / NST) - 1) & 1), abort_flag)) {
+                    if ((a.inject_after > 0 && i >= a.inject_after) ||
+                        (i >= NST && !wait_or_abort(smem_u32(empty + stg), (uint32_t)(((i / NST) - 1) & 1), abort_flag))) {
                         fail();
                         ok = false;
                         break;
                     }
                     const uint32_t dst = smem_u32(sm + stg * STAGE), bar = smem_u32(full + stg);
-                    const unsigned char *src = abase + (long long)(ci % NKC) * NPART * A_PART;
+                    const unsigned char *src = reinterpret_cast<const unsigned char *>(a.top) +
+                                               (((long long)code * NKC + (ci % NKC)) * 2 + hh) * A_CHUNK;
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(STAGE) : "memory");
                     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                                 :: "r"(dst), "l"(src), "r"(NPART * A_PART), "r"(bar) : "memory");
-                    const CUtensorMap *maps[NPART] = {&tm_hi, &tm_mid, &tm_lo};
+                                 :: "r"(dst), "l"(src), "r"(A_CHUNK), "r"(bar) : "memory");
+                    const CUtensorMap *maps[NPART] = {&tm_hi, &tm_lo};
 #pragma unroll
                     for (int p = 0; p < NPART; ++p)
                         asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
                                      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
-                                     :: "r"(dst + NPART * A_PART + p * B_PART), "l"(reinterpret_cast<uint64_t>(maps[p])),
+                                     :: "r"(dst + A_CHUNK + p * B_PART), "l"(reinterpret_cast<uint64_t>(maps[p])),
                                         "r"(kc), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar) : "memory");
                     last[stg] = i;
                 }
@@ -406,109 +513,140 @@ grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __
         __syncwarp();
     } else if (warp == 5) {
         if (lane == 0) {
-            // D = FP32, A = B = BF16, both K-major, N = NT, M = 128
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
-                                   ((uint32_t)(128 >> 4) << 24);
+            // D = FP32, A = B = FP16, both K-major, N = NT, M = 128
+            const uint32_t idesc = (1u << 4) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
             // descriptors of stage 0; stage s adds s * STAGE to the address field.
             // A: no swizzle, core matrices 128 B apart along K, 8-row groups (KC / 8) * 128 B
-            // apart; B: 32-byte swizzle, 8-row groups of 32-byte rows 256 B apart
+            // apart, K = 16 steps 256 B apart; B: 128-byte swizzle, 8-row groups of
+            // 128-byte rows 1024 B apart, K = 16 steps 32 B apart
             const uint32_t s0 = smem_u32(sm);
             const uint64_t dA = sdesc(s0, 128, (KC / 8) * 128, 0);
-            const uint64_t dB = sdesc(s0 + NPART * A_PART, 16, 256, 6);
+            const uint64_t dB = sdesc(s0 + A_CHUNK, 16, 1024, 2);
             long long i = 0, g = 0, last_mma = -1;
             bool ok = true;
-            for (int u = blockIdx.x; u < n_units && ok; u += G, ++g) {
-                const int c_begin = (u / n_tiles) * GW;
-                const int c_end = (c_begin + GW < NCH_ALL) ? c_begin + GW : NCH_ALL;
-                const int b = (int)(g & 1);
-                if (g >= 2 && !wait_or_abort(smem_u32(acc_empty + b), (uint32_t)(((g >> 1) - 1) & 1), abort_flag)) {
-                    fail();
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t dcol = tmem + (uint32_t)b * 2 * NT;
-                for (int ci = c_begin; ci < c_end; ++ci, ++i) {
-                    const int stg = (int)(i % NST);
-                    if (!wait_or_abort(smem_u32(full + stg), (uint32_t)((i / NST) & 1), abort_flag)) {
+            for (int u = blockIdx.x; u < n_units && ok; u += G) {
+                const int ks = u / (2 * n_tiles);
+                const int c_begin = k_begin(ks) * NKC, c_end = k_begin(ks + 1) * NKC;
+                for (int gb = c_begin; gb < c_end && ok; gb += GW, ++g) {
+                    const int ge = (gb + GW < c_end) ? gb + GW : c_end;
+                    const int b = (int)(g & 1);
+                    if (g >= 2 && !wait_or_abort(smem_u32(acc_empty + b), (uint32_t)(((g >> 1) - 1) & 1), abort_flag)) {
                         fail();
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint64_t so = (uint64_t)((stg * STAGE) >> 4);
-                    // six products of the parts, (hi, hi) first; the rows of half h
-                    // start (128 / 8) * (KC / 8) * 128 bytes into each A part
-                    constexpr int PA[6] = {0, 0, 1, 0, 2, 1}, PB[6] = {0, 1, 0, 2, 0, 1};
-#pragma unroll
-                    for (int h = 0; h < 2; ++h)
-#pragma unroll
-                        for (int t = 0; t < 6; ++t) {
-                            const uint64_t ad = dA + so + ((PA[t] * A_PART + h * (A_PART / 2)) >> 4);
-                            const uint64_t bd = dB + so + ((PB[t] * B_PART) >> 4);
-                            const uint32_t d = dcol + h * NT;
-                            const uint32_t acc = (ci == c_begin && t == 0) ? 0u : 1u;
-                            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
-                                         :: "r"(d), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                    const uint32_t d = tmem + (uint32_t)b * NT;
+                    for (int ci = gb; ci < ge; ++ci, ++i) {
+                        const int stg = (int)(i % NST);
+                        if (!wait_or_abort(smem_u32(full + stg), (uint32_t)((i / NST) & 1), abort_flag)) {
+                            fail();
+                            ok = false;
+                            break;
                         }
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        const uint64_t so = (uint64_t)((stg * STAGE) >> 4);
+                        // per K = 16 step, three products of the parts: hi*hi, hi*lo, lo*hi
+                        constexpr int PA[3] = {0, 0, 1}, PB[3] = {0, 1, 0};
+#pragma unroll
+                        for (int kk = 0; kk < KC / UK; ++kk)
+#pragma unroll
+                            for (int t = 0; t < 3; ++t) {
+                                const uint64_t ad = dA + so + ((PA[t] * A_PART + kk * (UK / 8) * 128) >> 4);
+                                const uint64_t bd = dB + so + ((PB[t] * B_PART + kk * UK * 2) >> 4);
+                                const uint32_t acc = (ci == gb && kk == 0 && t == 0) ? 0u : 1u;
+                                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                                             :: "r"(d), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                            }
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                     :: "r"(smem_u32(empty + stg)) : "memory");
+                        last_mma = i;
+                    }
+                    if (!ok) break;
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                                 :: "r"(smem_u32(empty + stg)) : "memory");
-                    last_mma = i;
+                                 :: "r"(smem_u32(acc_full + b)) : "memory");
                 }
-                if (!ok) break;
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             :: "r"(smem_u32(acc_full + b)) : "memory");
             }
             // drain: the MMAs issued have completed before the CTA frees its memory
             if (last_mma >= 0 && !wait_bounded(smem_u32(empty + last_mma % NST), (uint32_t)((last_mma / NST) & 1))) drain_fail();
         }
         __syncwarp();
     } else {
+        // epilogue: warp w owns TMEM lanes (operator rows) 32 w .. 32 w + 31
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
         long long g = 0;
-        for (int u = blockIdx.x; u < n_units; u += G, ++g) {
-            const int tile_g = u % n_tiles;
-            const int b = (int)(g & 1);
-            bool ok = true;
-            if (lane == 0) ok = wait_or_abort(smem_u32(acc_full + b), (uint32_t)((g >> 1) & 1), abort_flag);
-            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-            if (!ok) {
-                if (lane == 0) fail();
-                break;
+        bool ok = true;
+        for (int u = blockIdx.x; u < n_units && ok; u += G) {
+            const int tile_g = u % n_tiles, hh = (u / n_tiles) & 1, ks = u / (2 * n_tiles);
+            const int c_begin = k_begin(ks) * NKC, c_end = k_begin(ks + 1) * NKC;
+            bool first = true;
+            for (int gb = c_begin; gb < c_end; gb += GW, ++g) {
+                const int b = (int)(g & 1);
+                bool got = true;
+                if (lane == 0) got = wait_or_abort(smem_u32(acc_full + b), (uint32_t)((g >> 1) & 1), abort_flag);
+                got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+                if (!got) {
+                    if (lane == 0) fail();
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                for (int c0 = 0; c0 < NT; c0 += 32) {
+                    uint32_t va[32], vh[32], vl[32];
+                    tmem_ld32(tmem + lane_base + (uint32_t)(b * NT + c0), va);
+                    if (!first) {
+                        tmem_ld32(tmem + lane_base + (uint32_t)(2 * NT + c0), vh);
+                        tmem_ld32(tmem + lane_base + (uint32_t)(3 * NT + c0), vl);
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float x = __uint_as_float(va[j]);
+                        float hi = x, lo = 0.f;
+                        if (!first) {
+                            // two-sum: h0 + x = s + err exactly, then lo += err
+                            const float h0 = __uint_as_float(vh[j]);
+                            const float s = __fadd_rn(h0, x);
+                            const float bb = __fsub_rn(s, h0);
+                            const float err = __fadd_rn(__fsub_rn(h0, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+                            hi = s;
+                            lo = __fadd_rn(__uint_as_float(vl[j]), err);
+                        }
+                        vh[j] = __float_as_uint(hi);
+                        vl[j] = __float_as_uint(lo);
+                    }
+                    tmem_st32(tmem + lane_base + (uint32_t)(2 * NT + c0), vh);
+                    tmem_st32(tmem + lane_base + (uint32_t)(3 * NT + c0), vl);
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(acc_empty + b)) : "memory");
+                first = false;
             }
-            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (!ok) break;
+            // the unit's sums, once, in FP64: row = operator row, column = target
             const int cls = tile_g / tiles, tile = tile_g % tiles;
             const int bx = (cls >> 2) & 1, by = (cls >> 1) & 1, bz = cls & 1;
             const int tx = tile / (tpd * tpz), ty = (tile / tpz) % tpd, tz = tile % tpz;
-            for (int hc = 0; hc < 2 * (NT / 64); ++hc) {
-                const int h = hc / (NT / 64), c0 = (hc % (NT / 64)) * 64;
-                uint32_t v[64];
-                const uint32_t ta = tmem + (uint32_t)b * 2 * NT + h * NT + c0 + ((uint32_t)(warp * 32) << 16);
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x64.b32 "
-                             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-                             "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
-                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-                               "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-                               "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]),
-                               "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]),
-                               "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]),
-                               "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]),
-                               "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
-                             : "r"(ta));
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-                const int row = h * 128 + warp * 32 + lane;
+            const int row = hh * HROWS + warp * 32 + lane;
+            double *yk = a.ypart + (long long)ks * nb * KD + row;
+            for (int c0 = 0; c0 < NT; c0 += 32) {
+                uint32_t vh[32], vl[32];
+                tmem_ld32(tmem + lane_base + (uint32_t)(2 * NT + c0), vh);
+                tmem_ld32(tmem + lane_base + (uint32_t)(3 * NT + c0), vl);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int jj = 0; jj < 64; ++jj) {
+                for (int jj = 0; jj < 32; ++jj) {
                     const int j = c0 + jj;
                     const int x = 2 * (tx * 4 + (j / (4 * TZ))) + bx;
                     const int y = 2 * (ty * 4 + ((j / TZ) & 3)) + by;
                     const int z = 2 * (tz * TZ + (j % TZ)) + bz;
-                    atomicAdd(a.y + (((long long)x * ns + y) * ns + z) * KD + row, (double)__uint_as_float(v[jj]));
+                    yk[(((long long)x * ns + y) * ns + z) * KD] =
+                        (double)__uint_as_float(vh[jj]) + (double)__uint_as_float(vl[jj]);
                 }
             }
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(acc_empty + b)) : "memory");
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -524,13 +662,16 @@ grid_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tm_hi, const __
 struct sfmm_grid_ctx {
     sfmm_handle h = nullptr;
     int P = GP, nside = 0;
-    unsigned short *top = nullptr;           // operators, pre-tiled hi|mid|lo BF16 chunks
-    unsigned short *xhi = nullptr, *xmid = nullptr, *xlo = nullptr;   // packed sources (BF16 parts)
-    double *y = nullptr;                     // FP64 accumulators
+    __half *top = nullptr;                   // operators, pre-tiled hi|lo FP16 chunks
+    __half *xhi = nullptr, *xlo = nullptr;   // packed sources (FP16 parts)
+    double *ypart = nullptr;                 // FP64 sums of the two K halves
     double *c = nullptr;                     // sqrt((n-m)!(n+m)!) on the device
-    std::vector<double> ch;                  // and on the host
-    CUtensorMap tm_hi, tm_mid, tm_lo;        // 5-D maps of the source parts (tile boxes)
+    int *row_exp = nullptr;                  // power-of-two scale of every operator row
+    unsigned int *xmax = nullptr;            // largest |x| of the current call (float bits)
+    std::vector<double> ch;                  // c on the host
+    CUtensorMap tm_hi, tm_lo;                // 5-D maps of the source parts (tile boxes)
     int nt = 0;                              // targets per tile: 128 or 64
+    long long inject_after = 0;              // fault injection, see sfmm_grid_inject_timeout
 };
 
 namespace {
@@ -540,16 +681,16 @@ using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 // map of the parity-split halo grid [8][nh/2][nh/2][nh/2][KD] (innermost last)
-// with boxes of KC BF16 values x tz x 4 x 4 boxes x 1 parity class, 32-byte swizzle
-bool encode_source_map(EncodeTiled enc, CUtensorMap *m, unsigned short *base, int nside, int tz) {
+// with boxes of KC FP16 values x tz x 4 x 4 boxes x 1 parity class, 128-byte swizzle
+bool encode_source_map(EncodeTiled enc, CUtensorMap *m, __half *base, int nside, int tz) {
     const cuuint64_t nh2 = (cuuint64_t)(nside + 6) / 2;
     const cuuint64_t dims[5] = {(cuuint64_t)KD, nh2, nh2, nh2, 8};
-    const cuuint64_t row = (cuuint64_t)KD * sizeof(unsigned short);
+    const cuuint64_t row = (cuuint64_t)KD * sizeof(__half);
     const cuuint64_t strides[4] = {row, row * nh2, row * nh2 * nh2, row * nh2 * nh2 * nh2};
     const cuuint32_t box[5] = {(cuuint32_t)KC, (cuuint32_t)tz, 4, 4, 1};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5, base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -568,14 +709,15 @@ sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out) {
     g->h = h;
     g->nside = nside;
     const long long nh = nside + 6;
-    const size_t op_bytes = (size_t)NCODE * NKC * NPART * A_PART;
-    const size_t x_bytes = sizeof(unsigned short) * (size_t)(nh * nh * nh) * KD;
+    const size_t op_bytes = (size_t)NCODE * NKC * 2 * A_CHUNK;
+    const size_t x_bytes = sizeof(__half) * (size_t)(nh * nh * nh) * KD;
     bool ok = cudaMalloc(&g->top, op_bytes) == cudaSuccess &&
               cudaMalloc(&g->xhi, x_bytes) == cudaSuccess &&
-              cudaMalloc(&g->xmid, x_bytes) == cudaSuccess &&
               cudaMalloc(&g->xlo, x_bytes) == cudaSuccess &&
-              cudaMalloc(&g->y, sizeof(double) * (size_t)nside * nside * nside * KD) == cudaSuccess &&
-              cudaMalloc(&g->c, sizeof(double) * GP * (GP + 1) / 2) == cudaSuccess;
+              cudaMalloc(&g->ypart, sizeof(double) * KS * (size_t)nside * nside * nside * KD) == cudaSuccess &&
+              cudaMalloc(&g->c, sizeof(double) * GP * (GP + 1) / 2) == cudaSuccess &&
+              cudaMalloc(&g->row_exp, sizeof(int) * KD) == cudaSuccess &&
+              cudaMalloc(&g->xmax, sizeof(unsigned int)) == cudaSuccess;
     if (!ok) { sfmm_grid_destroy(g); return SFMM_ERR_NOMEM; }
     cudaMemset(g->top, 0, op_bytes);
     std::vector<double> c(GP * (GP + 1) / 2);
@@ -587,6 +729,33 @@ sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out) {
     }
     cudaMemcpy(g->c, c.data(), sizeof(double) * c.size(), cudaMemcpyHostToDevice);
     g->ch = c;
+    {
+        short pos_of_e[KD], e_of_pos[SOLID];
+        unsigned char sidx_of_e[KD], sidx_of_pos[SOLID];
+        for (int e = 0; e < KD; ++e) {
+            int n, m;
+            bool im;
+            reduced_index(e, &n, &m, &im);
+            pos_of_e[e] = (short)(n * (n + 1) + (im ? n + 1 + m : m));
+            sidx_of_e[e] = (unsigned char)(n * (n + 1) / 2 + m);
+        }
+        for (int p = 0; p < SOLID; ++p) {
+            int n = 0;
+            while ((n + 1) * (n + 2) <= p) ++n;
+            const int q = p - n * (n + 1);
+            const bool im = q > n;
+            const int m = im ? q - n - 1 : q;
+            e_of_pos[p] = (short)((im && m == 0) ? -1 : n * n + (im ? n + m : m));
+            sidx_of_pos[p] = (unsigned char)(n * (n + 1) / 2 + m);
+        }
+        if (cudaMemcpyToSymbol(c_pos_of_e, pos_of_e, sizeof(pos_of_e)) != cudaSuccess ||
+            cudaMemcpyToSymbol(c_sidx_of_e, sidx_of_e, sizeof(sidx_of_e)) != cudaSuccess ||
+            cudaMemcpyToSymbol(c_e_of_pos, e_of_pos, sizeof(e_of_pos)) != cudaSuccess ||
+            cudaMemcpyToSymbol(c_sidx_of_pos, sidx_of_pos, sizeof(sidx_of_pos)) != cudaSuccess) {
+            sfmm_grid_destroy(g);
+            return SFMM_ERR_CUDA;
+        }
+    }
     // operators: M2L (FP64, rotation-based) of the KD basis vectors for every offset
     std::vector<int> codes;
     for (int dx = -3; dx <= 3; ++dx)
@@ -608,7 +777,7 @@ sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out) {
     const long long count = (long long)ncodes * KD;
     std::vector<double> shift(3 * count);
     std::vector<long long> pin(count), pout(count);
-    double *dbasis = nullptr, *dL = nullptr, *dshift = nullptr;
+    double *dbasis = nullptr, *dL = nullptr, *dshift = nullptr, *drowmax = nullptr;
     long long *dpin = nullptr, *dpout = nullptr;
     int *dcodes = nullptr;
     ok = cudaMalloc(&dbasis, sizeof(double) * basis.size()) == cudaSuccess &&
@@ -616,7 +785,8 @@ sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out) {
          cudaMalloc(&dshift, sizeof(double) * shift.size()) == cudaSuccess &&
          cudaMalloc(&dpin, sizeof(long long) * count) == cudaSuccess &&
          cudaMalloc(&dpout, sizeof(long long) * count) == cudaSuccess &&
-         cudaMalloc(&dcodes, sizeof(int) * ncodes) == cudaSuccess;
+         cudaMalloc(&dcodes, sizeof(int) * ncodes) == cudaSuccess &&
+         cudaMalloc(&drowmax, sizeof(double) * KD) == cudaSuccess;
     sfmm_status st = ok ? SFMM_OK : SFMM_ERR_NOMEM;
     if (st == SFMM_OK) {
         for (int k = 0; k < ncodes; ++k) {
@@ -640,7 +810,24 @@ sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out) {
                             reinterpret_cast<void *const *>(dpout), dshift, GP, GP, count, 0, nullptr);
     }
     if (st == SFMM_OK) {
-        operator_kernel<<<1024, 256>>>(dL, dcodes, ncodes, g->c, g->top);
+        // operator row scales 2^e: the row's largest entry times 2^e lies in
+        // [2^(OP_ROW_EXP-1), 2^OP_ROW_EXP)
+        operator_rowmax_kernel<<<KD, 256>>>(dL, ncodes, g->c, drowmax);
+        std::vector<double> rowmax(KD);
+        std::vector<int> rexp(KD, 0);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(rowmax.data(), drowmax, sizeof(double) * KD, cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = SFMM_ERR_CUDA;
+        for (int e = 0; e < KD && st == SFMM_OK; ++e) {
+            int ex = 0;
+            if (rowmax[e] > 0.0) std::frexp(rowmax[e], &ex);      // rowmax < 2^ex
+            rexp[e] = OP_ROW_EXP - ex;
+        }
+        if (st == SFMM_OK && cudaMemcpy(g->row_exp, rexp.data(), sizeof(int) * KD, cudaMemcpyHostToDevice) != cudaSuccess)
+            st = SFMM_ERR_CUDA;
+    }
+    if (st == SFMM_OK) {
+        operator_kernel<<<1024, 256>>>(dL, dcodes, ncodes, g->c, g->row_exp, g->top);
         if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) st = SFMM_ERR_CUDA;
     }
     cudaFree(dbasis);
@@ -649,6 +836,7 @@ sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out) {
     cudaFree(dpin);
     cudaFree(dpout);
     cudaFree(dcodes);
+    cudaFree(drowmax);
     if (st == SFMM_OK &&
         (cudaFuncSetAttribute(grid_gemm_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_gemm<64>()) != cudaSuccess ||
          cudaFuncSetAttribute(grid_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_gemm<128>()) != cudaSuccess))
@@ -660,7 +848,6 @@ sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out) {
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
             q != cudaDriverEntryPointSuccess || fn == nullptr ||
             !encode_source_map(reinterpret_cast<EncodeTiled>(fn), &g->tm_hi, g->xhi, nside, g->nt / 16) ||
-            !encode_source_map(reinterpret_cast<EncodeTiled>(fn), &g->tm_mid, g->xmid, nside, g->nt / 16) ||
             !encode_source_map(reinterpret_cast<EncodeTiled>(fn), &g->tm_lo, g->xlo, nside, g->nt / 16))
             st = SFMM_ERR_CUDA;
     }
@@ -677,11 +864,18 @@ sfmm_status sfmm_grid_destroy(sfmm_grid g) {
     cudaDeviceSynchronize();
     cudaFree(g->top);
     cudaFree(g->xhi);
-    cudaFree(g->xmid);
     cudaFree(g->xlo);
-    cudaFree(g->y);
+    cudaFree(g->ypart);
     cudaFree(g->c);
+    cudaFree(g->row_exp);
+    cudaFree(g->xmax);
     delete g;
+    return SFMM_OK;
+}
+
+sfmm_status sfmm_grid_inject_timeout(sfmm_grid g, long long after_chunks) {
+    if (g == nullptr || after_chunks < 0) return SFMM_ERR_ARG;
+    g->inject_after = after_chunks;
     return SFMM_OK;
 }
 
@@ -690,8 +884,6 @@ sfmm_status sfmm_grid_m2l(sfmm_grid g, double box_size, const void *M, void *L, 
     if (g == nullptr || M == nullptr || L == nullptr || !(box_size > 0)) return SFMM_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int ns = g->nside;
-    if (cudaMemsetAsync(g->y, 0, sizeof(double) * (size_t)ns * ns * ns * KD, s) != cudaSuccess)
-        return SFMM_ERR_CUDA;
     Scales sp, su;
     for (int n = 0; n < GP; ++n) {
         const double hn = std::pow(box_size, n);
@@ -700,16 +892,22 @@ sfmm_status sfmm_grid_m2l(sfmm_grid g, double box_size, const void *M, void *L, 
             su.s[n * (n + 1) / 2 + m] = g->ch[n * (n + 1) / 2 + m] / hn;
         }
     }
-    pack_kernel<<<2048, 256, 0, s>>>(reinterpret_cast<const double *>(M), ns, sp, g->xhi, g->xmid, g->xlo);
+    const long long nb = (long long)ns * ns * ns;
+    const int nh2 = (ns + 6) / 2;
+    if (cudaMemsetAsync(g->xmax, 0, sizeof(unsigned int), s) != cudaSuccess) return SFMM_ERR_CUDA;
+    const int nhb = 8 * nh2 * nh2 * nh2;
+    xmax_kernel<<<(unsigned)(nb < 2048 ? nb : 2048), SOLID_THREADS, 0, s>>>(reinterpret_cast<const double *>(M), nb, sp, g->xmax);
+    pack_kernel<<<nhb < 4096 ? nhb : 4096, KD, 0, s>>>(reinterpret_cast<const double *>(M), ns, sp, g->xmax, g->xhi, g->xlo);
     // tiles of 4 x 4 x (nt / 16) same-octant targets; one persistent CTA per SM
-    // deals the (K slab, tile) units round-robin
-    GemmArgs a{g->top, g->y, ns, g->h->d_status};
+    // deals the (tile, row half, K half) units round-robin
+    GemmArgs a{g->top, g->ypart, ns, g->h->d_status, g->inject_after};
     const int ctas = g->h->sm_count > 0 ? g->h->sm_count : 1;
     if (g->nt == 128)
-        grid_gemm_kernel<128><<<ctas, 192, smem_gemm<128>(), s>>>(a, g->tm_hi, g->tm_mid, g->tm_lo);
+        grid_gemm_kernel<128><<<ctas, 192, smem_gemm<128>(), s>>>(a, g->tm_hi, g->tm_lo);
     else
-        grid_gemm_kernel<64><<<ctas, 192, smem_gemm<64>(), s>>>(a, g->tm_hi, g->tm_mid, g->tm_lo);
-    unpack_kernel<<<2048, 256, 0, s>>>(g->y, ns, su, reinterpret_cast<double *>(L), accumulate);
+        grid_gemm_kernel<64><<<ctas, 192, smem_gemm<64>(), s>>>(a, g->tm_hi, g->tm_lo);
+    unpack_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), SOLID_THREADS, 0, s>>>(g->ypart, ns, su, g->row_exp, g->xmax,
+                                                                           reinterpret_cast<double *>(L), accumulate);
     return cudaGetLastError() == cudaSuccess ? SFMM_OK : SFMM_ERR_CUDA;
 }
 

@@ -53,6 +53,7 @@ _SIGS = {
     "sfmm_grid_create": (_i, [_vp, _i, _i, ctypes.POINTER(_vp)]),
     "sfmm_grid_m2l": (_i, [_vp, ctypes.c_double, _vp, _vp, _i, _vp]),
     "sfmm_grid_destroy": (_i, [_vp]),
+    "sfmm_grid_inject_timeout": (_i, [_vp, _ll]),
     "sfmm_host_swap_matrices": (_i, [_i, _dp, _dp]),
     "sfmm_host_ztranslate": (_i, [_i, _i, _i, _dp]),
 }
@@ -225,6 +226,10 @@ class Grid:
     def m2l(self, box_size, M, L, accumulate=False, stream=None):
         _check(_lib.sfmm_grid_m2l(self._g, float(box_size), _addr(M), _addr(L),
                                   int(bool(accumulate)), _stream(stream)), "sfmm_grid_m2l")
+
+    def inject_timeout(self, after_chunks):
+        """sfmm_grid_inject_timeout: fault injection for the time-out path (tests)."""
+        _check(_lib.sfmm_grid_inject_timeout(self._g, int(after_chunks)), "sfmm_grid_inject_timeout")
 
     def close(self):
         if getattr(self, "_g", None):

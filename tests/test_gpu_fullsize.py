@@ -9,7 +9,7 @@ the M2M-combined multipoles of its children at the same order).
   level-3 targets.  A second run of the same launches gives bitwise the same
   locals (the lists kernels add in a fixed order).
 * The same tree at P = 16 through the tensor-core grid M2L of level 5
-  (three-part BF16 split, FP64 target sums): 8 sampled targets at the FP32-class
+  (two-part FP16 split, float-float target sums): 8 sampled targets at the FP32-class
   tolerance.
 * The largest serving request (10^6 M2L at order 30, FP64 and FP32).
 * The mixed-order pass on the 2 M-point Plummer sphere: 3 sampled targets."""
