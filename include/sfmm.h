@@ -199,6 +199,49 @@ sfmm_status sfmm_translate_lists_multi(sfmm_handle h, const sfmm_list_class *cla
                                        void *const *out, int accumulate, sfmm_stream stream);
 
 /*
+ * A whole translation pass in one persistent launch (Sec. 1.1: M2M, M2L and
+ * L2L of mixed orders are the operations of an FMM pass; an adaptive pass is
+ * M2M level by level, the M2L lists, L2L level by level).  Each class is one
+ * (op, p_in, p_out) applied to its own target-major lists, with the semantics
+ * of sfmm_translate_lists for those arrays (src: nnz device pointers to solids
+ * of order p_in; shift: 3 nnz reals, r = target centre - source centre;
+ * offsets: n_targets + 1 non-decreasing long long; out: n_targets distinct
+ * device pointers to solids of order p_out; accumulate as there;
+ * lanes_per_target as in sfmm_list_class).  Classes carry a phase number and
+ * come in non-decreasing phase order: every class of phase k starts only after
+ * every class of the phases before it has finished (so a phase may read what
+ * earlier phases wrote), while the classes of one phase run concurrently and
+ * must not write the same target.  The launch is cooperative: all its CTAs
+ * are resident, and they meet at a grid barrier between phases; a barrier
+ * that is not reached within 2 s sets bit 32 of the status word
+ * (sfmm_sync_status) and the launch ends.  Rotated solids and partial sums
+ * live in the handle's global scratch, which must hold one slot for the
+ * largest orders (sfmm_reserve_scratch).  classes is a HOST array (copied into
+ * the launch).  1 <= n_classes <= SFMM_MAX_PASS_CLASSES, at most
+ * SFMM_MAX_PASS_PHASES distinct phases.
+ * Errors: SFMM_ERR_ARG, SFMM_ERR_ORDER, SFMM_ERR_UNSUPPORTED (no scratch, too
+ * many phases), SFMM_ERR_CUDA (including a device that cannot run the
+ * cooperative launch).
+ */
+#define SFMM_MAX_PASS_CLASSES 320
+#define SFMM_MAX_PASS_PHASES 64
+typedef struct {
+    int op;                   /* sfmm_op */
+    int p_in, p_out;
+    int lanes_per_target;     /* 0 (32 for M2L, 8 for M2M, L2L), 1, 2, 4, 8, 16 or 32 */
+    int phase;                /* non-decreasing over the classes of a call */
+    int accumulate;
+    long long n_targets;
+    const void *const *src;
+    const void *shift;
+    const long long *offsets;
+    void *const *out;
+} sfmm_pass_class;
+
+sfmm_status sfmm_translate_pass(sfmm_handle h, const sfmm_pass_class *classes, int n_classes,
+                                sfmm_stream stream);
+
+/*
  * Launch policies (the tile-size choice of Sec. 3.2, made per order on the
  * GPU): which kernel variant serves (op, p_in, p_out) on this handle and how
  * many warps a block has (0 = automatic).

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -18,6 +19,8 @@
 using namespace sfmm;
 
 static_assert(SFMM_MAX_CLASSES == MAX_CLASSES, "class table sizes of the ABI and the kernel differ");
+static_assert(SFMM_MAX_PASS_CLASSES == MAX_PASS_CLASSES && SFMM_MAX_PASS_PHASES == MAX_PASS_PHASES,
+              "pass table sizes of the ABI and the kernel differ");
 
 
 namespace {
@@ -406,6 +409,8 @@ sfmm_status sfmm_create(int P_max, sfmm_dtype dtype, sfmm_handle *out) {
     sfmm_status st = dtype == SFMM_F64 ? upload<double>(ht, h, &h->t64) : upload<float>(ht, h, &h->t32);
     if (st == SFMM_OK && cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess) st = SFMM_ERR_NOMEM;
     if (st == SFMM_OK && cudaMalloc(&h->d_work, sizeof(unsigned long long)) != cudaSuccess) st = SFMM_ERR_NOMEM;
+    if (st == SFMM_OK && cudaMalloc(&h->d_pass, 2 * MAX_PASS_PHASES * sizeof(unsigned long long)) != cudaSuccess)
+        st = SFMM_ERR_NOMEM;
     if (st == SFMM_OK && cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) st = SFMM_ERR_CUDA;
     if (st == SFMM_OK) {
         const size_t esz = dtype == SFMM_F64 ? sizeof(double) : sizeof(float);
@@ -432,6 +437,7 @@ sfmm_status sfmm_create(int P_max, sfmm_dtype dtype, sfmm_handle *out) {
         cudaFree(h->d_tables);
         cudaFree(h->d_status);
         cudaFree(h->d_work);
+        cudaFree(h->d_pass);
         cudaFree(h->d_scratch);
         if (h->scratch_free) cudaEventDestroy(h->scratch_free);
         delete h;
@@ -447,6 +453,7 @@ sfmm_status sfmm_destroy(sfmm_handle h) {
     cudaFree(h->d_tables);
     cudaFree(h->d_status);
     cudaFree(h->d_work);
+    cudaFree(h->d_pass);
     cudaFree(h->d_scratch);
     if (h->scratch_free) cudaEventDestroy(h->scratch_free);
     delete h;
@@ -634,6 +641,99 @@ static sfmm_status launch_multi(sfmm_handle h, const sfmm_list_class *classes, i
                     h->d_status);
     return cudaGetLastError() == cudaSuccess ? SFMM_OK : SFMM_ERR_CUDA;
 }
+
+// One launch for a whole pass: classes grouped into phases (sfmm_translate_pass).
+template <typename T>
+static sfmm_status launch_pass(sfmm_handle h, const sfmm_pass_class *classes, int n, cudaStream_t stream,
+                               const DevTables<T> &tb) {
+    std::unique_ptr<PassParams> pp(new (std::nothrow) PassParams());
+    if (!pp) return SFMM_ERR_NOMEM;
+    int xs = 0, rs = 0, nph = 0;
+    long long chunks = 0;
+    for (int k = 0; k < n; ++k) {
+        const sfmm_pass_class &c = classes[k];
+        if (k == 0 || c.phase != classes[k - 1].phase) {
+            if (nph == MAX_PASS_PHASES) return SFMM_ERR_UNSUPPORTED;
+            if (nph > 0) {
+                pp->ph[nph - 1].chunk_end = chunks;
+                pp->ph[nph - 1].class_end = k;
+            }
+            pp->ph[nph].chunk_begin = chunks;
+            pp->ph[nph].class_begin = k;
+            ++nph;
+        }
+        PassClass &m = pp->c[k];
+        m.src = static_cast<const void *>(c.src);
+        m.shift = c.shift;
+        m.offsets = c.offsets;
+        m.out = static_cast<void *>(const_cast<void **>(c.out));
+        m.n_targets = c.n_targets;
+        m.op = c.op;
+        m.p_in = c.p_in;
+        m.p_out = c.p_out;
+        m.g = c.lanes_per_target > 0 ? c.lanes_per_target : default_lanes(c.op);
+        m.accumulate = c.accumulate != 0;
+        m.chunk_begin = chunks;
+        const int per_chunk = WARP / m.g;
+        chunks += (c.n_targets + per_chunk - 1) / per_chunk;
+        const int xk = x_elems(c.p_in) + (m.g > 1 ? c.p_out * (c.p_out + 1) : 0);
+        xs = xs > xk ? xs : xk;
+        rs = rs > row_elems(c.p_in, c.p_out) ? rs : row_elems(c.p_in, c.p_out);
+    }
+    pp->ph[nph - 1].chunk_end = chunks;
+    pp->ph[nph - 1].class_end = n;
+    pp->n_phases = nph;
+    pp->x_slot = xs;
+    pp->row_slot = rs;
+    const size_t per_warp = (size_t)rs * WARP * sizeof(T);
+    const size_t slot = (size_t)xs * WARP * sizeof(T);
+    if (h->d_scratch == nullptr || per_warp > h->smem_optin || slot > h->scratch_bytes)
+        return SFMM_ERR_UNSUPPORTED;
+    int w = (int)(h->smem_optin / 2 / per_warp);
+    if (w < 1) w = 1;
+    if (w > 4) w = 4;
+    const long long slots = (long long)(h->scratch_bytes / slot);
+    if (w > slots) w = (int)slots;
+    Geometry g;
+    g.xg = true;
+    g.warps = w;
+    g.smem = (size_t)w * per_warp;
+    long long blocks = slots / w;
+    const long long resident = pass_resident_blocks<T>(h, g);
+    if (resident < 0) return SFMM_ERR_CUDA;
+    if (blocks > resident) blocks = resident;
+    if (blocks < 1) return SFMM_ERR_UNSUPPORTED;
+    g.blocks = blocks;
+    ScratchGuard guard(h, stream, true);
+    if (cudaMemsetAsync(h->d_pass, 0, 2 * MAX_PASS_PHASES * sizeof(unsigned long long), stream) != cudaSuccess)
+        return SFMM_ERR_CUDA;
+    if (pass_launch<T>(h, g, stream, tb, *pp, reinterpret_cast<T *>(h->d_scratch), h->d_pass, h->d_status) != cudaSuccess)
+        return SFMM_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? SFMM_OK : SFMM_ERR_CUDA;
+}
+
+extern "C" {
+
+sfmm_status sfmm_translate_pass(sfmm_handle h, const sfmm_pass_class *classes, int n_classes,
+                                sfmm_stream stream) {
+    if (h == nullptr || classes == nullptr || n_classes < 1 || n_classes > SFMM_MAX_PASS_CLASSES)
+        return SFMM_ERR_ARG;
+    for (int k = 0; k < n_classes; ++k) {
+        const sfmm_pass_class &c = classes[k];
+        if (c.op != SFMM_M2M && c.op != SFMM_M2L && c.op != SFMM_L2L) return SFMM_ERR_ARG;
+        if (c.n_targets < 0 || (k > 0 && c.phase < classes[k - 1].phase)) return SFMM_ERR_ARG;
+        const int g = c.lanes_per_target;
+        if (g != 0 && g != 1 && g != 2 && g != 4 && g != 8 && g != 16 && g != 32) return SFMM_ERR_ARG;
+        if (c.p_in < 1 || c.p_out < 1 || c.p_in > h->Pmax || c.p_out > h->Pmax) return SFMM_ERR_ORDER;
+        if (c.n_targets > 0 && (c.src == nullptr || c.shift == nullptr || c.offsets == nullptr || c.out == nullptr))
+            return SFMM_ERR_ARG;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (h->dtype == SFMM_F64) return launch_pass<double>(h, classes, n_classes, s, h->t64);
+    return launch_pass<float>(h, classes, n_classes, s, h->t32);
+}
+
+}  // extern "C"
 
 extern "C" {
 

@@ -18,6 +18,7 @@ struct sfmm_ctx {
     void *d_tables = nullptr;   // one allocation holding every table
     int *d_status = nullptr;    // device status word (atomicOr by kernels)
     unsigned long long *d_work = nullptr;   // chunk counter of the group-lists launches (with the scratch)
+    unsigned long long *d_pass = nullptr;   // per-phase chunk and barrier counters of the pass kernel
     sfmm::DevTables<double> t64{};
     sfmm::DevTables<float> t32{};
     // global scratch for orders whose rotated solid does not fit in shared

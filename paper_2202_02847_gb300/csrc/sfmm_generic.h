@@ -44,6 +44,14 @@ void multi_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, con
                   const MultiParams &mp, const T *const *src, const T *shift, const long long *offsets,
                   T *const *out, int acc, T *scratch, int *status);
 
+// the phased pass kernel: a cooperative launch of `blocks` (all resident);
+// returns the launch's error code
+template <typename T>
+cudaError_t pass_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
+                        const PassParams &pp, T *scratch, unsigned long long *counters, int *status);
+template <typename T>
+long long pass_resident_blocks(const sfmm_ctx *h, const Geometry &g);
+
 // raise the dynamic shared memory limit of the kernels of one unit
 template <typename T, int OP>
 void set_generic_attrs(size_t smem);

@@ -71,6 +71,31 @@ void multi_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, con
     k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, mp, src, shift, offsets, out, acc, scratch, status);
 }
 
+template <typename T>
+long long pass_resident_blocks(const sfmm_ctx *h, const Geometry &g) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<T>, g.warps * WARP, g.smem) != cudaSuccess)
+        return -1;
+    return (long long)nb * h->sm_count;
+}
+
+template <typename T>
+cudaError_t pass_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
+                        const PassParams &pp, T *scratch, unsigned long long *counters, int *status) {
+    (void)h;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)g.blocks);
+    cfg.blockDim = dim3((unsigned)(g.warps * WARP));
+    cfg.dynamicSmemBytes = g.smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, pass_kernel<T>, tb, pp, scratch, counters, status);
+}
+
 template <typename T, int OP>
 void set_generic_attrs(size_t smem) {
     attr(batch_kernel<T, OP, false>, smem);
@@ -83,6 +108,7 @@ void set_generic_attrs(size_t smem) {
 template <typename T>
 void set_multi_attrs(size_t smem) {
     attr(multi_lists_kernel<T>, smem);
+    attr(pass_kernel<T>, smem);
 }
 
 #if defined(SFMM_GENERIC_OP)
@@ -104,6 +130,9 @@ template void multi_launch<GT>(const sfmm_ctx *, const Geometry &, cudaStream_t,
                                const MultiParams &, const GT *const *, const GT *, const long long *,
                                GT *const *, int, GT *, int *);
 template void set_multi_attrs<GT>(size_t);
+template cudaError_t pass_launch<GT>(const sfmm_ctx *, const Geometry &, cudaStream_t, const DevTables<GT> &,
+                                     const PassParams &, GT *, unsigned long long *, int *);
+template long long pass_resident_blocks<GT>(const sfmm_ctx *, const Geometry &);
 #endif
 
 }  // namespace sfmm

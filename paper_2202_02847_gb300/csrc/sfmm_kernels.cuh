@@ -247,12 +247,21 @@ struct PowSeq<double> {
 
 // Output sink: overwrite or add one coefficient of the result (a solid in
 // memory, or a lane's interleaved slot in the scratch).
-template <typename T>
+// Loads of solids: CG = true reads through L2 only (ld.global.cg), for data
+// that other SMs write during the same launch (the phased pass kernel);
+// otherwise ordinary loads.
+template <bool CG, typename T>
+__device__ __forceinline__ T ldd(const T *p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
+template <bool CG, typename T>
 __device__ __forceinline__ void put(T *dst, T v, bool add) {
-    if (add) v += *dst;
+    if (add) v += ldd<CG>(dst);
     *dst = v;
 }
-template <typename T>
+template <bool CG, typename T>
 __device__ __forceinline__ void put(LaneArr<T> dst, T v, bool add) {
     if (add) v += dst[0];
     dst[0] = v;
@@ -261,7 +270,7 @@ __device__ __forceinline__ void put(LaneArr<T> dst, T v, bool add) {
 // One translation computed by the calling thread (Sec. 3.4 steps 1-4, with
 // the z-axis translation of the op).  `buf` is this lane's shared memory of
 // lane_elems(p_in, p_out) elements.  add = accumulate into dst.
-template <typename T, int OP, bool PT, typename D>
+template <typename T, int OP, bool PT, bool CG, typename D>
 __device__ void translate_impl(const DevTables<T> &tb, int p_in, int p_out,
                                const T *__restrict__ src, const T *__restrict__ shift,
                                D dst, bool add, LaneArr<T> X, LaneArr<T> buf) {
@@ -287,7 +296,7 @@ __device__ void translate_impl(const DevTables<T> &tb, int p_in, int p_out,
             // zero shift: M2M / L2L are the identity (truncated or zero-padded)
             for (int n = 0; n < p_out; ++n)
                 for (int j = 0; j < 2 * (n + 1); ++j)
-                    put(dst + n * (n + 1) + j, n < p_in ? src[n * (n + 1) + j] : T(0), add);
+                    put<CG>(dst + n * (n + 1) + j, n < p_in ? ldd<CG>(src + n * (n + 1) + j) : T(0), add);
             return;
         }
     }
@@ -319,7 +328,7 @@ __device__ void translate_impl(const DevTables<T> &tb, int p_in, int p_out,
         PowSeq<T> pa(ca, sa);
         for (int m = 0; m <= n; ++m) {
             const T f = basis_factor(s, ldt(cf + m), p2);
-            const T re = row[m] * f, im = row[n + 1 + m] * f;
+            const T re = ldd<CG>(row + m) * f, im = ldd<CG>(row + n + 1 + m) * f;
             T pr, pi;
             if constexpr (ptab) { pr = PAre[m]; pi = PAim[m]; } else { pa.next(m, pr, pi); }
             Are[m] = re * pr - im * pi;
@@ -379,8 +388,8 @@ __device__ void translate_impl(const DevTables<T> &tb, int p_in, int p_out,
             const T re = Are[m] * f, im = Aim[m] * f;
             T pr, pi;
             if constexpr (ptab) { pr = PAre[m]; pi = PAim[m]; } else { pa.next(m, pr, pi); }
-            put(orow + m, fma_t(re, pr, im * pi), add);
-            put(orow + n + 1 + m, im * pr - re * pi, add);
+            put<CG>(orow + m, fma_t(re, pr, im * pi), add);
+            put<CG>(orow + n + 1 + m, im * pr - re * pi, add);
         }
         so *= step_out;
     }
@@ -390,14 +399,14 @@ __device__ void translate_impl(const DevTables<T> &tb, int p_in, int p_out,
 // TABLES = false always regenerates them (one code path: the multi-class
 // kernel, which serves all three ops, keeps its compile time down that way;
 // its row buffers are still sized by row_elems).
-template <typename T, int OP, bool TABLES = true, typename D>
+template <typename T, int OP, bool TABLES = true, bool CG = false, typename D>
 __device__ __forceinline__ void translate_one(const DevTables<T> &tb, int p_in, int p_out,
                                               const T *__restrict__ src, const T *__restrict__ shift,
                                               D dst, bool add, LaneArr<T> X, LaneArr<T> buf) {
     if (TABLES && power_tables(p_in, p_out))
-        translate_impl<T, OP, TABLES>(tb, p_in, p_out, src, shift, dst, add, X, buf);
+        translate_impl<T, OP, TABLES, CG>(tb, p_in, p_out, src, shift, dst, add, X, buf);
     else
-        translate_impl<T, OP, false>(tb, p_in, p_out, src, shift, dst, add, X, buf);
+        translate_impl<T, OP, false, CG>(tb, p_in, p_out, src, shift, dst, add, X, buf);
 }
 
 // ---------------------------------------------------------------- kernels
@@ -487,7 +496,7 @@ __global__ void __launch_bounds__(256, 1) lists_kernel(DevTables<T> tb, const T 
 // member mem adds the coefficients mem, mem + G, ... of the group's slots, in
 // lane order, into the target.  The order of the additions is fixed, so the
 // result does not depend on timing.
-template <typename T, int OP, bool TABLES = true>
+template <typename T, int OP, bool TABLES = true, bool CG = false>
 __device__ void group_chunk(const DevTables<T> &tb, int p_in, int p_out, int G, long long t,
                             long long t_end, const T *const *src, const T *shift,
                             const long long *offsets, T *const *out, int accumulate,
@@ -509,7 +518,7 @@ __device__ void group_chunk(const DevTables<T> &tb, int p_in, int p_out, int G, 
     for (long long j = j0 + mem; j < j1; j += G) {
         const T *s = src[j];
         if (s == nullptr) { atomicOr(status, STATUS_NULL_POINTER); continue; }
-        translate_one<T, OP, TABLES>(tb, p_in, p_out, s, shift + 3 * j, Y, any, X, buf);
+        translate_one<T, OP, TABLES, CG>(tb, p_in, p_out, s, shift + 3 * j, Y, any, X, buf);
         any = true;
     }
     const unsigned has = __ballot_sync(0xffffffffu, any);
@@ -521,7 +530,7 @@ __device__ void group_chunk(const DevTables<T> &tb, int p_in, int p_out, int G, 
             T acc = T(0);
             for (int i = 0; i < G; ++i)
                 if ((has >> (q0 + i)) & 1u) acc += Y0.p[(size_t)e * WARP + q0 + i];
-            dst[e] = accumulate ? dst[e] + acc : acc;
+            dst[e] = accumulate ? ldd<CG>(dst + e) + acc : acc;
         }
     }
     __syncwarp();                                       // slots are reused by the next chunk
@@ -628,6 +637,129 @@ __global__ void __launch_bounds__(256, 1) multi_lists_kernel(DevTables<T> tb, Mu
             else translate_one<T, OP_L2L, false>(tb, cl.p_in, cl.p_out, s, shift + 3 * j, dst, add, X, buf);
             add = true;
         }
+    }
+}
+
+// A whole translation pass in one persistent launch: phases run one after the
+// other, and inside a phase warps take chunks of its classes from the phase's
+// counter (as in multi_lists_kernel).  Every class carries its own target-major
+// lists.  Between phases the CTAs meet at a grid barrier (the launch is
+// cooperative, so every CTA is resident); solids written in one phase are read
+// in later phases by other SMs, so all reads of solids go through L2 (CG).
+constexpr int MAX_PASS_CLASSES = 320;
+constexpr int MAX_PASS_PHASES = 64;
+enum { STATUS_PASS_TIMEOUT = 32 };
+struct PassClass {
+    const void *src;             // nnz pointers to input solids
+    const void *shift;           // 3 nnz reals
+    const long long *offsets;    // n_targets + 1
+    void *out;                   // n_targets pointers to output solids
+    long long n_targets;
+    long long chunk_begin;       // first chunk of the class in the launch's numbering
+    int op, p_in, p_out, g, accumulate, pad;
+};
+struct PassPhase {
+    long long chunk_begin, chunk_end;
+    int class_begin, class_end;
+};
+struct PassParams {
+    int n_phases;
+    int x_slot;                  // scratch elements per lane
+    int row_slot;                // shared elements per lane
+    PassPhase ph[MAX_PASS_PHASES];
+    PassClass c[MAX_PASS_CLASSES];
+};
+
+// wait until *ctr reaches target (acquire at GPU scope); bounded by 2^26 polls
+// and 2 s
+__device__ __forceinline__ bool wait_count(unsigned long long *ctr, unsigned long long target) {
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (int it = 0; it < (1 << 26); ++it) {
+        unsigned long long v;
+        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+        if (v >= target) return true;
+        if ((it & 63) == 63) {
+            unsigned long long t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t - t0 > 2000000000ull) return false;
+        }
+        __nanosleep(64);
+    }
+    return false;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 1) pass_kernel(DevTables<T> tb, const __grid_constant__ PassParams pp,
+                                                      T *scratch, unsigned long long *counters, int *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & (WARP - 1), warp = threadIdx.x / WARP;
+    const long long slot = (long long)blockIdx.x * (blockDim.x / WARP) + warp;
+    LaneArr<T> X{scratch + slot * pp.x_slot * WARP + lane};
+    LaneArr<T> buf{reinterpret_cast<T *>(smem_raw) + (size_t)warp * pp.row_slot * WARP + lane};
+    for (int ph = 0; ph < pp.n_phases; ++ph) {
+        const long long c0 = pp.ph[ph].chunk_begin, nch = pp.ph[ph].chunk_end - c0;
+        for (;;) {
+            long long c = 0;
+            if (lane == 0) c = (long long)atomicAdd(counters + ph, 1ull);
+            c = __shfl_sync(0xffffffffu, c, 0);
+            if (c >= nch) break;
+            c += c0;
+            int k = pp.ph[ph].class_begin, hi = pp.ph[ph].class_end - 1;   // last class with chunk_begin <= c
+            while (k < hi) {
+                const int mid = (k + hi + 1) >> 1;
+                if (pp.c[mid].chunk_begin <= c) k = mid; else hi = mid - 1;
+            }
+            const PassClass &cl = pp.c[k];
+            const int op = cl.op, p_in = cl.p_in, p_out = cl.p_out, g = cl.g, acc = cl.accumulate;
+            const T *const *src = reinterpret_cast<const T *const *>(cl.src);
+            const T *shift = reinterpret_cast<const T *>(cl.shift);
+            const long long *offsets = cl.offsets;
+            T *const *out = reinterpret_cast<T *const *>(cl.out);
+            if (g > 1) {
+                const long long tg = (c - cl.chunk_begin) * (WARP / g) + lane / g;
+                const LaneArr<T> Y = X + x_elems(p_in);
+                if (op == OP_M2M)
+                    group_chunk<T, OP_M2M, false, true>(tb, p_in, p_out, g, tg, cl.n_targets, src, shift, offsets, out, acc, X, Y, buf, status);
+                else if (op == OP_M2L)
+                    group_chunk<T, OP_M2L, false, true>(tb, p_in, p_out, g, tg, cl.n_targets, src, shift, offsets, out, acc, X, Y, buf, status);
+                else
+                    group_chunk<T, OP_L2L, false, true>(tb, p_in, p_out, g, tg, cl.n_targets, src, shift, offsets, out, acc, X, Y, buf, status);
+                continue;
+            }
+            const long long t = (c - cl.chunk_begin) * WARP + lane;
+            if (t >= cl.n_targets) continue;
+            T *dst = out[t];
+            const long long j0 = offsets[t], j1 = offsets[t + 1];
+            if (dst == nullptr) { atomicOr(status, STATUS_NULL_POINTER); continue; }
+            if (j1 < j0) { atomicOr(status, STATUS_BAD_OFFSETS); continue; }
+            bool add = acc != 0;
+            if (j0 == j1 && !add)
+                for (int e = 0; e < p_out * (p_out + 1); ++e) dst[e] = T(0);
+            for (long long j = j0; j < j1; ++j) {
+                const T *s = src[j];
+                if (s == nullptr) { atomicOr(status, STATUS_NULL_POINTER); continue; }
+                if (op == OP_M2M) translate_one<T, OP_M2M, false, true>(tb, p_in, p_out, s, shift + 3 * j, dst, add, X, buf);
+                else if (op == OP_M2L) translate_one<T, OP_M2L, false, true>(tb, p_in, p_out, s, shift + 3 * j, dst, add, X, buf);
+                else translate_one<T, OP_L2L, false, true>(tb, p_in, p_out, s, shift + 3 * j, dst, add, X, buf);
+                add = true;
+            }
+        }
+        if (ph + 1 == pp.n_phases) break;
+        // grid barrier: this CTA's writes of the phase are released before it
+        // arrives; the next phase starts once every CTA has arrived
+        __syncthreads();
+        int gave_up = 0;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(counters + MAX_PASS_PHASES + ph, 1ull);
+            if (!wait_count(counters + MAX_PASS_PHASES + ph, gridDim.x)) {
+                atomicOr(status, STATUS_PASS_TIMEOUT);
+                gave_up = 1;
+            }
+            __threadfence();
+        }
+        if (__syncthreads_or(gave_up)) return;
     }
 }
 

@@ -277,6 +277,7 @@ class AdaptivePass:
         self.counts = dict(m2m=int(sum(len(d["src"]) for d in self.m2m)), m2l=self.n_m2l,
                            l2l=int(sum(d["count"] for d in self.l2l)))
         pmax = int(self.P.max())
+        self._plans = {}
         if handle is not None:                    # None: build the plan only (host tests)
             sfmm.reserve_scratch(handle, pmax)
 
@@ -336,6 +337,47 @@ class AdaptivePass:
         self.upward(stream)
         self.m2l_all(stream)
         self.downward(stream)
+
+    def pass_plan(self, parts=("m2m", "m2l", "l2l")):
+        """The pass as phased classes for sfmm_translate_pass: one phase per M2M
+        level (deepest first, parents overwritten), one per M2L wave (the
+        wave's classes, accumulating), one per L2L level (each child a list of
+        its parent, accumulating).  Built once per choice of parts; the
+        arrays it points into are held by the pass object."""
+        key = tuple(parts)
+        if key in self._plans:
+            return self._plans[key]
+        cls, keep, ph = [], [], 0
+        if "m2m" in parts:
+            for d in self.m2m:
+                cls.append(("m2m", d["p_in"], d["p_out"], 8, ph, False, d["n"], d["src"], d["shift"],
+                            d["offsets"], d["out"]))
+                ph += 1
+        if "m2l" in parts:
+            for d in self.waves:
+                for op, pi, po, tb, te, g in d["classes"]:
+                    cls.append((op, pi, po, g, ph, True, te - tb, d["src"], d["shift"],
+                                d["offsets"][tb:], d["out"][tb:]))
+                ph += 1
+        if "l2l" in parts:
+            for d in self.l2l:
+                offs = torch.arange(d["count"] + 1, dtype=torch.int64, device=self.device)
+                keep.append(offs)
+                cls.append(("l2l", d["p_in"], d["p_out"], 1, ph, True, d["count"], d["inp"], d["shift"],
+                            offs, d["out"]))
+                ph += 1
+        plan = (sfmm.pass_classes(cls), keep, ph)
+        self._plans[key] = plan
+        return plan
+
+    def run_pass(self, parts=("m2m", "m2l", "l2l"), stream=None):
+        """The chosen parts of the pass as one persistent launch."""
+        sfmm.translate_pass(self.h, self.pass_plan(parts)[0], stream=stream)
+
+    def step_one_launch(self, stream=None):
+        """The whole pass (locals zeroed first) as one persistent launch."""
+        self.L.zero_()
+        self.run_pass(stream=stream)
 
     def launches_per_step(self):
         m2l = sum((len(d["classes"]) + sfmm.MAX_CLASSES - 1) // sfmm.MAX_CLASSES if d["fused"]

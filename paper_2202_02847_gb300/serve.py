@@ -102,7 +102,7 @@ class Arena:
 class TranslationServer:
     def __init__(self, P_max=30, pool_size=4096, n_shifts=1 << 20, arena_bytes=8 << 30,
                  n_streams=4, chunk=1 << 20, inflight_per_stream=2, device="cuda", seed=5,
-                 chunk_flop=2e9, age_limit_s=0.25):
+                 chunk_flop=1e9, age_limit_s=0.25):
         self.device = torch.device(device)
         self.P_max = P_max
         self.streams = [torch.cuda.Stream(self.device) for _ in range(n_streams)]
@@ -211,10 +211,11 @@ class TranslationServer:
 
     def _chunk_len(self, r):
         """Translations in the request's next chunk: about chunk_flop of work,
-        but at least one full wave of the batch kernel (wave translations) so
-        that a chunk alone keeps every SM busy, and at most `chunk`."""
+        but at least a quarter wave of the batch kernel (chunks of the four
+        streams overlap on the device, so four such chunks keep every SM
+        busy), and at most `chunk`."""
         per = translation_flop(r.p_in, r.p_out)
-        n = max(self.wave, int(self.chunk_flop // per))
+        n = max(self.wave // 4, int(self.chunk_flop // per))
         return max(1, min(n, self.chunk, r.count - r._next))
 
     def run(self, requests, keep_outputs=False):

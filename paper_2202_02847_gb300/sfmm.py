@@ -48,6 +48,7 @@ _SIGS = {
     "sfmm_sync_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
     "sfmm_translate_batch_noalloc": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _ll, _i, _vp]),
     "sfmm_translate_lists_multi": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp, _i, _vp]),
+    "sfmm_translate_pass": (_i, [_vp, _vp, _i, _vp]),
     "sfmm_set_policy": (_i, [_vp, _i, _i, _i, _i, _i]),
     "sfmm_reserve_scratch": (_i, [_vp, _i]),
     "sfmm_grid_create": (_i, [_vp, _i, _i, ctypes.POINTER(_vp)]),
@@ -201,6 +202,34 @@ def translate_lists_multi(h, classes, src, shift, offsets, out, accumulate=False
                                            _addr(shift), _addr(offsets), _addr(out),
                                            int(bool(accumulate)), _stream(stream)),
            "sfmm_translate_lists_multi")
+
+
+class PassClass(ctypes.Structure):
+    """sfmm_pass_class (include/sfmm.h)."""
+    _fields_ = [("op", _i), ("p_in", _i), ("p_out", _i), ("lanes_per_target", _i),
+                ("phase", _i), ("accumulate", _i), ("n_targets", _ll),
+                ("src", _vp), ("shift", _vp), ("offsets", _vp), ("out", _vp)]
+
+
+MAX_PASS_CLASSES = 320
+MAX_PASS_PHASES = 64
+
+
+def pass_classes(classes):
+    """Pack (op, p_in, p_out, lanes, phase, accumulate, n_targets, src, shift,
+    offsets, out) tuples (arrays as tensors or addresses) into the C array."""
+    arr = (PassClass * len(classes))()
+    for k, (op, pi, po, g, ph, acc, nt, src, shift, offs, out) in enumerate(classes):
+        arr[k] = PassClass(OPS.get(op, op), int(pi), int(po), int(g), int(ph), int(bool(acc)), int(nt),
+                           _addr(src), _addr(shift), _addr(offs), _addr(out))
+    return arr
+
+
+def translate_pass(h, classes, stream=None):
+    """sfmm_translate_pass: a whole pass of phased classes in one launch.
+    `classes` is the packed array of pass_classes()."""
+    _check(_lib.sfmm_translate_pass(h.ptr, ctypes.cast(classes, _vp), len(classes), _stream(stream)),
+           "sfmm_translate_pass")
 
 
 def set_policy(h, op, p_in, p_out, policy="auto", warps=0):

@@ -138,3 +138,67 @@ def test_policy_errors(setup):
     with pytest.raises(sfmm.SfmmError) as e:
         sfmm.set_policy(h, "m2l", 7, 99, "shared")
     assert e.value.code == 2
+
+
+def _check_all_nodes(ap, tree, P_node, got, want, kind, tol, what):
+    """Per-expansion check of every node's solid (grouped by order)."""
+    for P in np.unique(P_node):
+        nodes = np.nonzero(P_node == P)[0]
+        S = int(P) * (int(P) + 1)
+        idx = (ap.off[nodes][:, None] + np.arange(S)[None, :])
+        U.check_rows(got[idx], want[idx], int(P), kind, tol, a=np.sqrt(3.0) * tree.half[nodes],
+                     what=f"{what}, order {P}")
+
+
+def test_one_launch_pass_matches_the_multi_launch_pass(setup):
+    """The whole pass (M2M levels, M2L waves, L2L levels) as one persistent
+    launch with grid barriers between its phases gives, for every expansion,
+    the result of the pass as separate launches (within 1e-12), and bitwise
+    the same result on every run and under CUDA-graph replay."""
+    import torch
+    sfmm, ap, pts, q, tree, P_node, h = setup
+    ap.step()
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    refL, refM = ap.L.cpu().numpy(), ap.M.cpu().numpy()
+    ap.step_one_launch()
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    one = ap.L.clone()
+    _check_all_nodes(ap, tree, P_node, ap.M.cpu().numpy(), refM, "M", 1e-12, "M after the one-launch pass")
+    _check_all_nodes(ap, tree, P_node, one.cpu().numpy(), refL, "L", 1e-12, "L after the one-launch pass")
+    ap.step_one_launch()
+    torch.cuda.synchronize()
+    assert torch.equal(ap.L, one)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        ap.step_one_launch()
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        ap.step_one_launch()
+    ap.L.fill_(3.0)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    assert torch.equal(ap.L, one)
+
+
+def test_pass_rejects_bad_classes(setup):
+    import torch
+    sfmm, ap, pts, q, tree, P_node, h = setup
+    z = torch.zeros(4, dtype=torch.int64, device="cuda")
+    bad_phase = sfmm.pass_classes([("m2l", 4, 4, 1, 1, True, 1, z, z, z, z),
+                                   ("m2l", 4, 4, 1, 0, True, 1, z, z, z, z)])
+    with pytest.raises(sfmm.SfmmError) as e:
+        sfmm.translate_pass(h, bad_phase)
+    assert e.value.code == 1
+    bad_lanes = sfmm.pass_classes([("m2l", 4, 4, 3, 0, True, 1, z, z, z, z)])
+    with pytest.raises(sfmm.SfmmError) as e:
+        sfmm.translate_pass(h, bad_lanes)
+    assert e.value.code == 1
+    bad_order = sfmm.pass_classes([("m2l", 4, 99, 1, 0, True, 1, z, z, z, z)])
+    with pytest.raises(sfmm.SfmmError) as e:
+        sfmm.translate_pass(h, bad_order)
+    assert e.value.code == 2

@@ -195,4 +195,16 @@ def test_adaptive_plummer_2m_sampled_against_oracle(sf, orc):
         got = L[ap.off[t]:ap.off[t + 1]]
         U.check_rows(got, want, Po, "L", 1e-12, a=float(np.sqrt(3.0) * tree.half[t]),
                      what=f"target {t}")
+    # the upward pass and the M2L waves as one persistent launch: every target
+    # agrees with the separate launches checked above
+    ap.L.zero_()
+    ap.run_pass(("m2m", "m2l"))
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    L1 = ap.L.cpu().numpy()
+    for P in np.unique(P_node):
+        nodes = np.nonzero(P_node == P)[0]
+        idx = ap.off[nodes][:, None] + np.arange(int(P) * (int(P) + 1))[None, :]
+        U.check_rows(L1[idx], L[idx], int(P), "L", 1e-12, a=np.sqrt(3.0) * tree.half[nodes],
+                     what=f"one-launch pass, order {P}")
     h.close()
