@@ -334,7 +334,16 @@ __device__ __forceinline__ void translate_u(Sw<T> X, T x, T y, T z) {
 }
 
 // Copy the 32 solids of the warp's lanes from global memory into the
-// swizzled area (null pointer: zeros).  All 32 lanes take part.
+// swizzled area (null pointer: zeros).  All 32 lanes take part.  Every element
+// is an asynchronous global-to-shared copy (cp.async), so all of a round's
+// loads are in flight together and the warp waits once, instead of once per
+// batch of loads held in registers; the caller's __syncwarp() then publishes
+// the copies to the whole warp.
+template <typename T>
+__device__ __forceinline__ void copy_async(T *dst, const T *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;"
+                 :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src), "n"((int)sizeof(T)) : "memory");
+}
 template <typename T, int S>
 __device__ __forceinline__ void load_solids(Sw<T> X, const T *mine) {
 #pragma unroll 4
@@ -344,9 +353,13 @@ __device__ __forceinline__ void load_solids(Sw<T> X, const T *mine) {
 #pragma unroll
         for (int e0 = 0; e0 < S; e0 += 32) {
             const int e = e0 + X.lane;
-            if (e < S) X.at(e, j) = p ? __ldg(p + e) : T(0);
+            if (e < S) {
+                if (p) copy_async(&X.at(e, j), p + e);
+                else X.at(e, j) = T(0);
+            }
         }
     }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
 
 template <typename T, int P, int OP>
