@@ -206,9 +206,90 @@ __device__ __forceinline__ void columns_z(Sw<T> X) {
     }
 }
 
+// Tensor memory as per-lane storage (the lists kernel's running sums): a
+// warp reads and writes its own 32 lanes, `NC` consecutive 32-bit columns.
+template <int NC>
+__device__ __forceinline__ void tm_ld(uint32_t ta, uint32_t *r) {
+    if constexpr (NC >= 32) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                     "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                     "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                       "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                       "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                       "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                     : "r"(ta));
+        tm_ld<NC - 32>(ta + 32, r + 32);
+    } else if constexpr (NC >= 16) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                     "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                       "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                     : "r"(ta));
+        tm_ld<NC - 16>(ta + 16, r + 16);
+    } else if constexpr (NC >= 8) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                     : "r"(ta));
+        tm_ld<NC - 8>(ta + 8, r + 8);
+    } else if constexpr (NC >= 4) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(ta));
+        tm_ld<NC - 4>(ta + 4, r + 4);
+    }
+}
+template <int NC>
+__device__ __forceinline__ void tm_st(uint32_t ta, const uint32_t *r) {
+    if constexpr (NC >= 32) {
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+                     "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                     "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+                     :: "r"(ta), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+                        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+                        "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+                        "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+                     : "memory");
+        tm_st<NC - 32>(ta + 32, r + 32);
+    } else if constexpr (NC >= 16) {
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+                     "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                     :: "r"(ta), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+                        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+                     : "memory");
+        tm_st<NC - 16>(ta + 16, r + 16);
+    } else if constexpr (NC >= 8) {
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                     :: "r"(ta), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                     : "memory");
+        tm_st<NC - 8>(ta + 8, r + 8);
+    } else if constexpr (NC >= 4) {
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};"
+                     :: "r"(ta), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]) : "memory");
+        tm_st<NC - 4>(ta + 4, r + 4);
+    }
+}
+__device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ double tm_double(const uint32_t *w) { return __hiloint2double((int)w[1], (int)w[0]); }
+__device__ __forceinline__ void tm_put(uint32_t *w, double v) {
+    w[0] = (uint32_t)__double2loint(v);
+    w[1] = (uint32_t)__double2hiint(v);
+}
+
+// Running sums of the lists kernel in tensor memory: `ta` addresses the lane's
+// solid (element e at columns 2e, 2e+1); `first` = the target's first round.
+struct TAcc {
+    uint32_t ta;
+    bool first;
+};
+
 // Output row N: swap, rotate -beta, swap, rotate -alpha, undo basis and scaling.
-template <typename T, int P, int OP, int N>
-__device__ __forceinline__ void rows_out(Sw<T> X, const Powers<T, P> &pw, T so, T step) {
+// ACC (FP64 M2L lists kernel): instead of storing the row into X, add it to the
+// lane's running sum in tensor memory, folded into the last rotation's
+// multiply-adds (the sums over a target's list are then added across lanes
+// once per target, not once per round).
+template <typename T, int P, int OP, int N, bool ACC = false>
+__device__ __forceinline__ void rows_out(Sw<T> X, const Powers<T, P> &pw, T so, T step, TAcc acc = TAcc{0, true}) {
     if constexpr (N < P) {
         constexpr int o = N * (N + 1);
         T ar[N + 1], ai[N + 1], br[N + 1], bi[N + 1];
@@ -225,17 +306,42 @@ __device__ __forceinline__ void rows_out(Sw<T> X, const Powers<T, P> &pw, T so, 
         // m = 0: the rotation is the identity and the swap leaves Im = 0.
         if constexpr (OP == OP_M2L) swap_u<T, N, OFF_FO, OFF_GO>(br, bi, ar, ai);
         else swap_u<T, N>(br, bi, ar, ai);
+        if constexpr (ACC) {
+            static_assert(sizeof(T) == 8, "tensor-memory sums hold FP64 solids");
+            constexpr int NC = 4 * (N + 1);                 // 2 (N+1) doubles
+            uint32_t w[NC];
+            if (!acc.first) {
+                tm_ld<NC>(acc.ta + 2 * o, w);
+                tm_wait_ld();
+            } else {
 #pragma unroll
-        for (int m = 0; m <= N; ++m) {
-            const T f = (OP == OP_M2L) ? so : so * ct<T>((OP == OP_M2M ? OFF_IC : OFF_C) + N * (N + 1) / 2 + m);
-            if (m == 0) {
-                X[o] = ar[0] * f;
-                X[o + N + 1] = T(0);
-                continue;
+                for (int c = 0; c < NC; ++c) w[c] = 0u;
             }
-            const T re = ar[m] * f, im = ai[m] * f;
-            X[o + m] = fma_t(re, pw.ar[m], im * pw.ai[m]);
-            X[o + N + 1 + m] = im * pw.ar[m] - re * pw.ai[m];
+#pragma unroll
+            for (int m = 0; m <= N; ++m) {
+                const T f = (OP == OP_M2L) ? so : so * ct<T>((OP == OP_M2M ? OFF_IC : OFF_C) + N * (N + 1) / 2 + m);
+                if (m == 0) {
+                    tm_put(w, fma_t(ar[0], f, tm_double(w)));
+                    continue;
+                }
+                const T re = ar[m] * f, im = ai[m] * f;
+                tm_put(w + 2 * m, fma_t(re, pw.ar[m], fma_t(im, pw.ai[m], tm_double(w + 2 * m))));
+                tm_put(w + 2 * (N + 1 + m), fma_t(im, pw.ar[m], fma_t(-re, pw.ai[m], tm_double(w + 2 * (N + 1 + m)))));
+            }
+            tm_st<NC>(acc.ta + 2 * o, w);
+        } else {
+#pragma unroll
+            for (int m = 0; m <= N; ++m) {
+                const T f = (OP == OP_M2L) ? so : so * ct<T>((OP == OP_M2M ? OFF_IC : OFF_C) + N * (N + 1) / 2 + m);
+                if (m == 0) {
+                    X[o] = ar[0] * f;
+                    X[o + N + 1] = T(0);
+                    continue;
+                }
+                const T re = ar[m] * f, im = ai[m] * f;
+                X[o + m] = fma_t(re, pw.ar[m], im * pw.ai[m]);
+                X[o + N + 1 + m] = im * pw.ar[m] - re * pw.ai[m];
+            }
         }
     }
 }
@@ -260,9 +366,9 @@ __device__ __forceinline__ void step_switch(int st, Sw<T> X, const Powers<T, P> 
 // Only the M2L lists kernel pairs its steps: the batch kernels and the M2M and
 // L2L lists kernels have no registers to spare for a second row and the row
 // scales of every row (they would spill).
-template <typename T, int P, int OP, int K>
+template <typename T, int P, int OP, int K, bool ACC = false>
 __device__ __forceinline__ void step_switch2(int st, Sw<T> X, const Powers<T, P> &pw, const T *sin,
-                                             const T *sout) {
+                                             const T *sout, TAcc acc = TAcc{0, true}) {
     constexpr int H = (P + 1) / 2;
     if constexpr (K < 3 * H) {
         if (st == K) {
@@ -274,19 +380,19 @@ __device__ __forceinline__ void step_switch2(int st, Sw<T> X, const Powers<T, P>
                 columns_z<T, P, OP, i>(X);
                 if constexpr (j != i) columns_z<T, P, OP, j>(X);
             } else {
-                rows_out<T, P, OP, i>(X, pw, sout[i], T(0));
-                if constexpr (j != i) rows_out<T, P, OP, j>(X, pw, sout[j], T(0));
+                rows_out<T, P, OP, i, ACC>(X, pw, sout[i], T(0), acc);
+                if constexpr (j != i) rows_out<T, P, OP, j, ACC>(X, pw, sout[j], T(0), acc);
             }
         } else {
-            step_switch2<T, P, OP, K + 1>(st, X, pw, sin, sout);
+            step_switch2<T, P, OP, K + 1, ACC>(st, X, pw, sin, sout, acc);
         }
     }
 }
 
 // One translation of order P by the calling thread, in place on its solid X.
 // PAIRED (M2L in the lists kernel) runs two rows or columns per step.
-template <typename T, int P, int OP, bool PAIRED = false>
-__device__ __forceinline__ void translate_u(Sw<T> X, T x, T y, T z) {
+template <typename T, int P, int OP, bool PAIRED = false, bool ACC = false>
+__device__ __forceinline__ void translate_u(Sw<T> X, T x, T y, T z, TAcc acc = TAcc{0, true}) {
     const T rho2 = x * x + y * y;
     const T R = sqrt_t(rho2 + z * z);
     if (OP != OP_M2L && !(R > T(0))) return;            // zero shift: identity
@@ -321,7 +427,7 @@ __device__ __forceinline__ void translate_u(Sw<T> X, T x, T y, T z) {
 #pragma unroll
         for (int n = 1; n < P; ++n) { sin[n] = sin[n - 1] * step_in; sout[n] = sout[n - 1] * step_out; }
 #pragma unroll 1
-        for (int st = 0; st < 3 * ((P + 1) / 2); ++st) step_switch2<T, P, OP, 0>(st, X, pw, sin, sout);
+        for (int st = 0; st < 3 * ((P + 1) / 2); ++st) step_switch2<T, P, OP, 0, ACC>(st, X, pw, sin, sout, acc);
     } else {
         T s = s0, so = T(1);
 #pragma unroll 1
@@ -472,6 +578,103 @@ __global__ void __launch_bounds__(256, 1) ulists_kernel(const T *const *src, con
             }
         }
     }
+}
+
+// The lane sums of a target, from tensor memory back into the lane's solid
+// area X (rows N .. P-1), for the cross-lane reduction.
+template <typename T, int P, int N>
+__device__ __forceinline__ void flush_rows(Sw<T> X, uint32_t ta) {
+    if constexpr (N < P) {
+        constexpr int o = N * (N + 1), NC = 4 * (N + 1);
+        uint32_t w[NC];
+        tm_ld<NC>(ta + 2 * o, w);
+        tm_wait_ld();
+#pragma unroll
+        for (int k = 0; k < 2 * (N + 1); ++k) X[o + k] = tm_double(w + 2 * k);
+        flush_rows<T, P, N + 1>(X, ta);
+    }
+}
+
+// FP64 M2L interaction lists, one target per warp, with each lane's running sum
+// of its translations kept in tensor memory (free in this kernel: 256 KB per
+// SM, a warp's sums take 2 P(P+1) columns of its lane quadrant).  The last
+// rotation of every output row adds into the sum with its multiply-adds, and
+// the 32 lanes' sums are added in lane order once per target; the list is
+// summed per lane in round order.  `tcols` = tensor-memory columns of the CTA
+// (a power of two >= ceil(warps / 4) * 2 P(P+1)); the launch checks that the
+// CTAs resident on an SM fit in its 512 columns.
+template <typename T, int P>
+__global__ void __launch_bounds__(256, 1) ulists_acc_kernel(const T *const *src, const T *shift,
+                                                            const long long *offsets, T *const *out,
+                                                            long long n_targets, int accumulate,
+                                                            int *status, int tcols) {
+    constexpr int S = P * (P + 1);
+    constexpr int NA = (S + 31) / 32;          // coefficients per lane in the reduction
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    Sw<T> X{reinterpret_cast<T *>(smem_raw) + (size_t)warp * S * XSTRIDE, lane};
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem_raw + (size_t)nwarps * S * XSTRIDE * sizeof(T));
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"((uint32_t)__cvta_generic_to_shared(tslot)), "r"(tcols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t ta = *tslot + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 2 * S);
+    const long long nw = (long long)gridDim.x * nwarps;
+    const long long w = (long long)blockIdx.x * nwarps + warp;
+    for (long long k = 0; k * nw < n_targets; ++k) {
+        const long long t = deal_chunk(k, nw, w);
+        if (t >= n_targets) continue;
+        long long j0 = offsets[t], j1 = offsets[t + 1];
+        if (j1 < j0) {
+            if (lane == 0) atomicOr(status, STATUS_BAD_OFFSETS);
+            j1 = j0;
+        }
+        const int rounds = (int)((j1 - j0 + 31) / 32);
+        for (int r = 0; r < rounds; ++r) {
+            const long long j = j0 + (long long)r * 32 + lane;
+            const T *s = (j < j1) ? src[j] : nullptr;
+            if (j < j1 && s == nullptr) atomicOr(status, STATUS_NULL_POINTER);
+            load_solids<T, S>(X, s);
+            __syncwarp();
+            T x = T(0), y = T(0), z = T(1);
+            if (s) { x = shift[3 * j]; y = shift[3 * j + 1]; z = shift[3 * j + 2]; }
+            if (r > 0) tm_wait_st();                    // the previous round's sums are written
+            translate_u<T, P, OP_M2L, true, true>(X, x, y, z, TAcc{ta, r == 0});
+            __syncwarp();
+        }
+        if (rounds > 0) {
+            tm_wait_st();
+            flush_rows<T, P, 0>(X, ta);
+            __syncwarp();
+        }
+        T *dst = out[t];
+        if (dst == nullptr) {
+            if (lane == 0) atomicOr(status, STATUS_NULL_POINTER);
+        } else {
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                const int e = lane + a * 32;
+                if (e < S) {
+                    T v = T(0);
+                    if (rounds > 0) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) v += X.at(e, i);
+                    }
+                    dst[e] = accumulate ? dst[e] + v : v;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    tm_wait_st();
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(*tslot), "r"(tcols));
 }
 
 }  // namespace unrolled

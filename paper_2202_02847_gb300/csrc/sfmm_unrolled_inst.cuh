@@ -36,6 +36,7 @@ void set_attrs_t(size_t smem) {
     attr(ulists_kernel<T, P, OP_M2M, 8>, smem);
     attr(ulists_kernel<T, P, OP_M2L, 32>, smem);
     attr(ulists_kernel<T, P, OP_L2L, 8>, smem);
+    if constexpr (sizeof(T) == 8 && P <= 10) attr(ulists_acc_kernel<T, P>, smem);
 }
 
 void set_attrs(size_t smem) { set_attrs_t<Real>(smem); }
@@ -91,9 +92,43 @@ bool batch_t(const void *const *in, void *const *out, const void *shift, long lo
     return cudaGetLastError() == cudaSuccess;
 }
 
+// FP64 M2L lists with the lanes' running sums in tensor memory (orders up to
+// 10, where a warp's sums take at most 220 columns): launched when the
+// resident CTAs of an SM fit in its 512 columns, else false.
+template <typename T>
+bool lists_acc(const void *const *src, const void *shift, const long long *offsets,
+               void *const *out, long long n_targets, int accumulate, const Launch &L) {
+    if constexpr (sizeof(T) != 8 || P > 10) {
+        return false;
+    } else {
+        auto k = ulists_acc_kernel<T, P>;
+        int w;
+        size_t smem;
+        long long blocks;
+        if (!geometry<T>(k, L, n_targets, &w, &smem, &blocks)) return false;
+        smem += 16;                                  // the tensor-memory address slot
+        if (smem > L.smem_optin) return false;
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, w * 32, smem) != cudaSuccess || nb < 1)
+            return false;
+        const int need = ((w + 3) / 4) * 2 * S;
+        int tcols = 32;
+        while (tcols < need) tcols <<= 1;
+        if (tcols > 512 || nb * tcols > 512) return false;
+        const long long cap = (long long)nb * L.sm_count;
+        if (blocks > cap) blocks = cap;
+        k<<<(unsigned)blocks, w * 32, smem, L.stream>>>(
+            reinterpret_cast<const T *const *>(src), reinterpret_cast<const T *>(shift), offsets,
+            reinterpret_cast<T *const *>(out), n_targets, accumulate, L.status, tcols);
+        return cudaGetLastError() == cudaSuccess;
+    }
+}
+
 template <typename T, int OP, int G>
 bool lists_t(const void *const *src, const void *shift, const long long *offsets,
              void *const *out, long long n_targets, int accumulate, const Launch &L) {
+    if constexpr (OP == OP_M2L && G == 32)
+        if (lists_acc<T>(src, shift, offsets, out, n_targets, accumulate, L)) return true;
     auto k = ulists_kernel<T, P, OP, G>;
     int w;
     size_t smem;
