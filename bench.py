@@ -936,8 +936,8 @@ def main():
     roof = {"bound": "alu", "achieved": flop / m2l_mean_s / 1e12, "peak": peak / 1e12,
             "unit": "TFLOP/s", "frac": flop / m2l_mean_s / peak,
             "traffic": ncu_traffic() if args.dtype == "f64" and depth == DEPTH else None,
-            "kernel": f"ulists_kernel<{'double' if args.dtype == 'f64' else 'float'}, P=10, M2L, G=32>"
-                      " (one launch per step)",
+            "kernel": ("ulists_acc_kernel<double, 10> (running sums in tensor memory)" if args.dtype == "f64"
+                       else "ulists_kernel<float, 10, M2L, 32>") + " (one launch per step)",
             "m2l_ms_mean": m2l_mean_s * 1e3,
             "hbm_gbs_algorithmic": m2l_bytes(P, wbytes) * m2l_per_step / m2l_mean_s / 1e9}
 
