@@ -549,8 +549,10 @@ def run_serving(args):
     # the plain form: the same requests one at a time, each finished before the
     # next starts (no overlap on the device)
     t0 = time.perf_counter()
+    alone = {}
     for r in serve.make_requests(args.requests, seed=5):
-        srv.run([r])
+        for d in srv.run([r]):
+            alone[d.rid] = d.done_ms - 1e3 * d.arrival
     ser_s = time.perf_counter() - t0
     loads = {}
     for load in (0.5, 0.8):
@@ -559,7 +561,7 @@ def run_serving(args):
         t0 = time.perf_counter()
         done = srv.run(rr)
         wall = time.perf_counter() - t0
-        st = serve.latency_stats(done)
+        st = serve.latency_stats(done, alone)
         st["offered_rps"] = load * cap_rps
         st["translations_per_s"] = ntr / wall
         loads[str(load)] = st
@@ -575,16 +577,29 @@ def run_serving(args):
                    "requests_per_load_point": len(reqs), "streams": 4,
                    "chunk": "about 1e9 FLOP of translations, at least a quarter wave of the batch kernel",
                    "scheduling": "first-fit admission and shortest-remaining-work dealing, "
-                                 "both with a 0.25 s ageing bound; host clock",
+                                 "both with a 0.25 s ageing bound; requests whose remaining work "
+                                 "fits one chunk on a fifth stream of high priority, marshalling "
+                                 "on another; host clock",
                    "arena_gb": 24},
         "capacity": {"requests_per_s": cap_rps, "translations_per_s": ntr / cap_s,
                      "gflop_per_s": flop / cap_s / 1e9, "seconds": cap_s},
         "one_at_a_time": {"requests_per_s": len(reqs) / ser_s, "translations_per_s": ntr / ser_s,
-                          "seconds": ser_s},
+                          "seconds": ser_s,
+                          "p50_ms": float(np.percentile(list(alone.values()), 50)),
+                          "p99_ms": float(np.percentile(list(alone.values()), 99))},
         "latency": loads,
     }
     return line
 
+
+
+def hbm_peak():
+    """Measured HBM copy bandwidth in GB/s (MEASURED_PEAKS.json), else the
+    6,800 GB/s of an earlier GB300 measurement."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path)).get("hbm_gbs", 6800.0))
+    return 6800.0
 
 
 def fp_peak(dtype, nsm):
@@ -676,10 +691,17 @@ def per_order_sweep(orders, dtype, sample=12, seed=900):
         got = L[torch.tensor(pick, device="cuda")].double().cpu().numpy()
         err = U.rel_err_rows(got, want, P, "L")
         flop = m2l_flop(P) * n
-        kern = (f"ubatch_kernel<{'double' if dtype == 'f64' else 'float'},{P},M2L>"
-                if P in (6, 8, 10, 12) else "batch_kernel (generic)")
+        esz = 8 if dtype == "f64" else 4
+        nbytes = n * (2 * S * esz + 3 * esz + 16)      # solids in and out, shift, two pointers
+        if P in (6, 8, 10, 12):
+            kern = f"ubatch_kernel<{'double' if dtype == 'f64' else 'float'},{P},M2L>"
+        elif dtype == "f32" and P >= 16:
+            kern = "wbatch_kernel<float, M2L> (warp-cooperative, 4 solids per warp)"
+        else:
+            kern = "batch_kernel (generic, per-thread)"
         rec = {"P": P, "count": n, "ms": t * 1e3, "translations_per_s": n / t,
-               "tflops": flop / t / 1e12, "frac": flop / t / peak, "kernel": kern,
+               "tflops": flop / t / 1e12, "frac": flop / t / peak,
+               "hbm_gbs": nbytes / t / 1e9, "hbm_frac": nbytes / t / 1e9 / hbm_peak(), "kernel": kern,
                "rel_err_max": float(err.max()), "rel_err_median": float(np.median(err)),
                "oracle_sample": sample}
         if dtype == "f32":

@@ -245,9 +245,12 @@ sfmm_status sfmm_translate_pass(sfmm_handle h, const sfmm_pass_class *classes, i
  * Launch policies (the tile-size choice of Sec. 3.2, made per order on the
  * GPU): which kernel variant serves (op, p_in, p_out) on this handle and how
  * many warps a block has (0 = automatic).
- *   SFMM_POLICY_AUTO     - built-in choice: unrolled if compiled; else shared
- *                          memory while two blocks of two or more warps fit
- *                          per SM; else the global scratch (launches that use
+ *   SFMM_POLICY_AUTO     - built-in choice: unrolled if compiled; FP32 batch
+ *                          calls the warp-cooperative kernel for M2L of orders
+ *                          16..31 and M2M / L2L of orders 22..31; else shared
+ *                          memory while enough warps fit per SM (FP64: two
+ *                          blocks of two or more warps; FP32: eight warps);
+ *                          else the global scratch (launches that use
  *                          the scratch of one handle run one after another,
  *                          whatever their streams, through an event of the
  *                          handle; launches captured into a CUDA graph skip
@@ -257,6 +260,11 @@ sfmm_status sfmm_translate_pass(sfmm_handle h, const sfmm_pass_class *classes, i
  *   SFMM_POLICY_UNROLLED - fixed-order kernel; only p_in = p_out in {6,8,10,12}
  *   SFMM_POLICY_SHARED   - generic kernel, working set in shared memory
  *   SFMM_POLICY_GLOBAL   - generic kernel, rotated solid in the global scratch
+ *   SFMM_POLICY_WIDE     - warp-cooperative kernel (a warp translates 4 FP32 or
+ *                          2 FP64 solids together, its lanes splitting every
+ *                          row and column of Sec. 3.4 by coefficient index);
+ *                          batch calls with max(p_in, p_out) <= 31 only (lists
+ *                          calls take the AUTO choice)
  * Set policies before launching work with the handle (the table is not
  * synchronised against concurrent launches).  Errors: SFMM_ERR_ARG,
  * SFMM_ERR_ORDER, SFMM_ERR_UNSUPPORTED (variant cannot serve these orders).
@@ -265,7 +273,8 @@ typedef enum {
     SFMM_POLICY_AUTO = 0,
     SFMM_POLICY_UNROLLED = 1,
     SFMM_POLICY_SHARED = 2,
-    SFMM_POLICY_GLOBAL = 3
+    SFMM_POLICY_GLOBAL = 3,
+    SFMM_POLICY_WIDE = 4
 } sfmm_policy;
 
 sfmm_status sfmm_set_policy(sfmm_handle h, sfmm_op op, int p_in, int p_out,

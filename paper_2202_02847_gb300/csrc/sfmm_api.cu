@@ -39,11 +39,55 @@ void set_kernel_attrs(size_t smem) {
 }
 
 // Copy the host tables into one device buffer converted to T.
+// Transposed copies of the swap and z-translation tables for the
+// warp-cooperative kernels (layout in DevTables).
+struct WideHost {
+    std::vector<double> FT, GT, TzT[3];
+    std::vector<int> FTrow, GTrow;
+};
+
+WideHost transpose_tables(const HostTables &ht) {
+    WideHost w;
+    const int P = ht.Pmax;
+    for (int n = 0; n < P; ++n) {
+        const int fe = n / 2 + 1, fo = (n + 1) / 2, ge = (n + 1) / 2, go = n / 2;
+        w.FTrow.push_back((int)w.FT.size());
+        w.GTrow.push_back((int)w.GT.size());
+        const size_t f0 = w.FT.size(), g0 = w.GT.size();
+        w.FT.resize(f0 + (size_t)fe * (n + 1), 0.0);
+        w.GT.resize(g0 + (size_t)ge * n, 0.0);
+        int fm = 0, gm = 0;                 // packed start of row m
+        for (int m = 0; m <= n; ++m) {
+            const int cf = ((n + m) & 1) ? fo : fe;
+            for (int i = 0; i < cf; ++i) w.FT[f0 + (size_t)i * (n + 1) + m] = ht.F[ht.Frow[n] + fm + i];
+            fm += cf;
+            if (m >= 1) {
+                const int cg = ((n + m) & 1) ? go : ge;
+                for (int i = 0; i < cg; ++i) w.GT[g0 + (size_t)i * n + (m - 1)] = ht.G[ht.Grow[n] + gm + i];
+                gm += cg;
+            }
+        }
+    }
+    w.FTrow.push_back((int)w.FT.size());
+    w.GTrow.push_back((int)w.GT.size());
+    for (int op = 0; op < 3; ++op) {
+        w.TzT[op].assign(ht.Tz[op].size(), 0.0);
+        for (int m = 0; m < P; ++m) {
+            const long long off = ztrans_block_offset(P, m);
+            const int d = P - m;
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) w.TzT[op][off + (long long)b * d + a] = ht.Tz[op][off + (long long)a * d + b];
+        }
+    }
+    return w;
+}
+
 template <typename T>
 sfmm_status upload(const HostTables &ht, sfmm_ctx *h, DevTables<T> *dt) {
+    const WideHost wh = transpose_tables(ht);
     const size_t nF = ht.F.size(), nG = ht.G.size(), nc = ht.c.size(), nT = ht.Tz[0].size();
-    const size_t nreal = nF + nG + 2 * nc + 3 * nT;
-    const size_t nint = 2 * (size_t)(ht.Pmax + 1);
+    const size_t nreal = nF + nG + 2 * nc + 3 * nT + wh.FT.size() + wh.GT.size() + 3 * nT;
+    const size_t nint = 4 * (size_t)(ht.Pmax + 1);
     const size_t bytes = nreal * sizeof(T) + nint * sizeof(int) + 256;
     std::vector<unsigned char> host(bytes, 0);
     T *r = reinterpret_cast<T *>(host.data());
@@ -65,10 +109,14 @@ sfmm_status upload(const HostTables &ht, sfmm_ctx *h, DevTables<T> *dt) {
             }
     const size_t oF = put(ht.F), oG = put(ht.G), oc = put(cs), oic = put(ics);
     const size_t oT0 = put(ht.Tz[0]), oT1 = put(ht.Tz[1]), oT2 = put(ht.Tz[2]);
+    const size_t oFT = put(wh.FT), oGT = put(wh.GT);
+    const size_t oU0 = put(wh.TzT[0]), oU1 = put(wh.TzT[1]), oU2 = put(wh.TzT[2]);
     size_t ibyte = (o * sizeof(T) + 15) / 16 * 16;
     int *ip = reinterpret_cast<int *>(host.data() + ibyte);
     std::memcpy(ip, ht.Frow.data(), (ht.Pmax + 1) * sizeof(int));
     std::memcpy(ip + ht.Pmax + 1, ht.Grow.data(), (ht.Pmax + 1) * sizeof(int));
+    std::memcpy(ip + 2 * (ht.Pmax + 1), wh.FTrow.data(), (ht.Pmax + 1) * sizeof(int));
+    std::memcpy(ip + 3 * (ht.Pmax + 1), wh.GTrow.data(), (ht.Pmax + 1) * sizeof(int));
     if (cudaMalloc(&h->d_tables, bytes) != cudaSuccess) return SFMM_ERR_NOMEM;
     if (cudaMemcpy(h->d_tables, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess)
         return SFMM_ERR_CUDA;
@@ -83,6 +131,13 @@ sfmm_status upload(const HostTables &ht, sfmm_ctx *h, DevTables<T> *dt) {
     dt->Tz[2] = d + oT2;
     dt->Frow = di;
     dt->Grow = di + ht.Pmax + 1;
+    dt->FT = d + oFT;
+    dt->GT = d + oGT;
+    dt->TzT[0] = d + oU0;
+    dt->TzT[1] = d + oU1;
+    dt->TzT[2] = d + oU2;
+    dt->FTrow = di + 2 * (ht.Pmax + 1);
+    dt->GTrow = di + 3 * (ht.Pmax + 1);
     dt->Pmax = ht.Pmax;
     return SFMM_OK;
 }
@@ -143,7 +198,7 @@ sfmm_status fill_unrolled_constants(int dev, size_t smem_optin) {
 
 bool use_unrolled(const sfmm_ctx *h, int op, int p_in, int p_out) {
     const int pol = h->policy[op][p_in][p_out];
-    if (pol == SFMM_POLICY_SHARED || pol == SFMM_POLICY_GLOBAL) return false;
+    if (pol != SFMM_POLICY_AUTO && pol != SFMM_POLICY_UNROLLED) return false;
     return p_in == p_out && unrolled::compiled(p_in) && h->unrolled_ok;
 }
 
@@ -170,16 +225,20 @@ Geometry pick_geometry(const sfmm_ctx *h, int op, int p_in, int p_out, long long
     const size_t sz = sizeof(T);
     const int pol = h->policy[op][p_in][p_out];
     const int wfix = h->warps[op][p_in][p_out];
-    // AUTO keeps the working set in shared memory only while two blocks of at
-    // least two warps fit per SM (one warp per sub-partition; the FP64 pipe of a
-    // sub-partition idles without one), else it takes the global scratch
+    // AUTO keeps the working set in shared memory only while enough warps fit
+    // per SM, else it takes the global scratch.  FP64: two blocks of at least
+    // two warps (one warp per sub-partition; the FP64 pipe of a sub-partition
+    // idles without one).  FP32, bound by issue and latency rather than by a
+    // pipe: eight warps (below that the global scratch, cached in L1 and L2,
+    // is about twice as fast on GB300 at orders 13..16).
     bool shared = pol != SFMM_POLICY_GLOBAL && shared_only_fits<T>(h, p_in, p_out);
     if (shared && pol == SFMM_POLICY_AUTO) {
         const size_t pw = (size_t)(x_elems(p_in) + row_elems(p_in, p_out)) * WARP * sz;
         const size_t slot_g = (size_t)x_elems(p_in) * WARP * sz;
         const bool global_ok = h->d_scratch != nullptr && slot_g * 4 <= h->scratch_bytes &&
                                (size_t)row_elems(p_in, p_out) * WARP * sz <= h->smem_optin;
-        if (h->smem_optin / 2 / pw < 2 && global_ok) shared = false;
+        const bool few = sz == sizeof(float) ? h->smem_optin / pw < 8 : h->smem_optin / 2 / pw < 2;
+        if (few && global_ok) shared = false;
     }
     if (shared) {
         const size_t per_warp = (size_t)(x_elems(p_in) + row_elems(p_in, p_out)) * WARP * sz;
@@ -233,10 +292,37 @@ struct ScratchGuard {
     }
 };
 
+// The warp-cooperative kernel serves a batch call when the policy says so, or
+// under AUTO for FP32 M2L of orders 16..31 and FP32 M2M / L2L of orders
+// 22..31, where it is faster than the per-thread generic kernel with the
+// global scratch (measured on GB300: M2L 0.78 vs 0.86 ms at P = 16, 3.6 vs
+// 6.5 ms at P = 30; M2M / L2L even at P = 20, 1.3x faster at P = 30).  In FP64
+// the per-thread kernels keep the FP64 pipe busier and stay the default.
+template <typename T>
+bool wants_wide(const sfmm_ctx *h, int op, int p_in, int p_out) {
+    const int pol = h->policy[op][p_in][p_out];
+    if (pol == SFMM_POLICY_WIDE) return true;
+    const int Q = p_in > p_out ? p_in : p_out;
+    return pol == SFMM_POLICY_AUTO && sizeof(T) == sizeof(float) && Q <= wide_max_order() &&
+           Q >= (op == OP_M2L ? 16 : 22);
+}
+
 template <typename T>
 sfmm_status launch_batch(sfmm_handle h, int op, const void *const *in, void *const *out,
                          const void *shift, int p_in, int p_out, long long count,
                          int accumulate, cudaStream_t stream, const DevTables<T> &tb) {
+    if (wants_wide<T>(h, op, p_in, p_out)) {
+        auto I = reinterpret_cast<const T *const *>(in);
+        auto O = reinterpret_cast<T *const *>(out);
+        auto S = reinterpret_cast<const T *>(shift);
+        const int wf = h->warps[op][p_in][p_out];
+        bool ok;
+        if (op == OP_M2M) ok = wide_launch<T, OP_M2M>(h, wf, stream, tb, I, O, S, p_in, p_out, count, accumulate, h->d_status);
+        else if (op == OP_M2L) ok = wide_launch<T, OP_M2L>(h, wf, stream, tb, I, O, S, p_in, p_out, count, accumulate, h->d_status);
+        else ok = wide_launch<T, OP_L2L>(h, wf, stream, tb, I, O, S, p_in, p_out, count, accumulate, h->d_status);
+        if (ok) return cudaGetLastError() == cudaSuccess ? SFMM_OK : SFMM_ERR_CUDA;
+        if (h->policy[op][p_in][p_out] == SFMM_POLICY_WIDE) return SFMM_ERR_UNSUPPORTED;
+    }
     const Geometry g = pick_geometry<T>(h, op, p_in, p_out, count);
     if (g.warps < 1) return SFMM_ERR_UNSUPPORTED;
     if (g.blocks > 0x7fffffffLL) return SFMM_ERR_UNSUPPORTED;
@@ -545,7 +631,7 @@ sfmm_status sfmm_sync_status(sfmm_handle h, sfmm_stream stream, int *device_stat
 sfmm_status sfmm_set_policy(sfmm_handle h, sfmm_op op, int p_in, int p_out, sfmm_policy policy,
                             int warps_per_block) {
     if (h == nullptr || (op != SFMM_M2M && op != SFMM_M2L && op != SFMM_L2L)) return SFMM_ERR_ARG;
-    if (policy < SFMM_POLICY_AUTO || policy > SFMM_POLICY_GLOBAL || warps_per_block < 0 ||
+    if (policy < SFMM_POLICY_AUTO || policy > SFMM_POLICY_WIDE || warps_per_block < 0 ||
         warps_per_block > 8)
         return SFMM_ERR_ARG;
     if (p_in < 1 || p_out < 1 || p_in > h->Pmax || p_out > h->Pmax) return SFMM_ERR_ORDER;
@@ -557,6 +643,11 @@ sfmm_status sfmm_set_policy(sfmm_handle h, sfmm_op op, int p_in, int p_out, sfmm
         return SFMM_ERR_UNSUPPORTED;
     if (policy == SFMM_POLICY_GLOBAL &&
         (h->d_scratch == nullptr || (size_t)x_elems(p_in) * WARP * sz > h->scratch_bytes))
+        return SFMM_ERR_UNSUPPORTED;
+    if (policy == SFMM_POLICY_WIDE &&
+        ((p_in > p_out ? p_in : p_out) > wide_max_order() ||
+         (size_t)wide_warp_bytes(p_in > p_out ? p_in : p_out) * (warps_per_block > 0 ? warps_per_block : 1) >
+             h->smem_optin))
         return SFMM_ERR_UNSUPPORTED;
     h->policy[op][p_in][p_out] = (unsigned char)policy;
     h->warps[op][p_in][p_out] = (unsigned char)warps_per_block;

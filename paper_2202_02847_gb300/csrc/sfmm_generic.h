@@ -12,6 +12,7 @@
 
 #include "sfmm_ctx.h"
 #include "sfmm_kernels.cuh"
+#include "sfmm_wide.cuh"
 
 namespace sfmm {
 
@@ -43,6 +44,18 @@ template <typename T>
 void multi_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
                   const MultiParams &mp, const T *const *src, const T *shift, const long long *offsets,
                   T *const *out, int acc, T *scratch, int *status);
+
+inline int wide_max_order() { return wide::MAXQ; }
+inline size_t wide_warp_bytes(int Q) { return (size_t)wide::warp_units(Q) * 16; }
+
+// the warp-cooperative batch kernel (sfmm_wide.cuh): W solids per warp, the
+// block size (wfix warps, or 0: the one that leaves the most warps resident
+// per SM) and a persistent grid chosen here; false if it cannot serve these
+// orders (above 31, or a warp's area larger than the shared memory)
+template <typename T, int OP>
+bool wide_launch(const sfmm_ctx *h, int wfix, cudaStream_t stream, const DevTables<T> &tb,
+                 const T *const *I, T *const *O, const T *S, int p_in, int p_out, long long count,
+                 int acc, int *status);
 
 // the phased pass kernel: a cooperative launch of `blocks` (all resident);
 // returns the launch's error code

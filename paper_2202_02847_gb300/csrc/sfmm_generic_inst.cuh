@@ -3,6 +3,7 @@
 // multi-class kernel (SFMM_GENERIC_MULTI).  Included by one small translation
 // unit per case, so the units compile in parallel.
 #include "sfmm_generic.h"
+#include "sfmm_wide.cuh"
 
 #if !defined(SFMM_GENERIC_T) || !(defined(SFMM_GENERIC_OP) || defined(SFMM_GENERIC_MULTI))
 #error "define SFMM_GENERIC_T and SFMM_GENERIC_OP or SFMM_GENERIC_MULTI before including this file"
@@ -63,6 +64,37 @@ void glists_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, co
     k<<<(unsigned)resident_blocks(h, k, g), g.warps * WARP, g.smem, stream>>>(tb, Sp, S, offsets, O, p_in, p_out, nt, acc, G, scratch, work, status);
 }
 
+template <typename T, int OP>
+bool wide_launch(const sfmm_ctx *h, int wfix, cudaStream_t stream, const DevTables<T> &tb,
+                 const T *const *I, T *const *O, const T *S, int p_in, int p_out, long long count,
+                 int acc, int *status) {
+    const int Q = p_in > p_out ? p_in : p_out;
+    if (Q > wide::MAXQ) return false;
+    const size_t per_warp = (size_t)wide::warp_units(Q) * sizeof(wide::Pk<T>);
+    if (per_warp > h->smem_optin) return false;
+    if (count == 0) return true;
+    auto k = wide::wbatch_kernel<T, OP>;
+    int best_w = 0, best_nb = 0;
+    for (int w = 8; w >= 1; --w) {
+        if ((size_t)w * per_warp > h->smem_optin || (wfix > 0 && w != wfix)) continue;
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, w * WARP, (size_t)w * per_warp) != cudaSuccess)
+            nb = 0;
+        if (nb > 0 && w * nb > best_w * best_nb) {
+            best_w = w;
+            best_nb = nb;
+        }
+    }
+    if (best_w < 1) return false;
+    const long long groups = (count + wide::Pk<T>::W - 1) / wide::Pk<T>::W;
+    long long blocks = (groups + best_w - 1) / best_w;
+    const long long cap = (long long)best_nb * h->sm_count;
+    if (blocks > cap) blocks = cap;
+    k<<<(unsigned)blocks, best_w * WARP, (size_t)best_w * per_warp, stream>>>(tb, I, O, S, p_in, p_out, count, acc,
+                                                                             status);
+    return true;
+}
+
 template <typename T>
 void multi_launch(const sfmm_ctx *h, const Geometry &g, cudaStream_t stream, const DevTables<T> &tb,
                   const MultiParams &mp, const T *const *src, const T *shift, const long long *offsets,
@@ -103,6 +135,7 @@ void set_generic_attrs(size_t smem) {
     attr(lists_kernel<T, OP, false>, smem);
     attr(lists_kernel<T, OP, true>, smem);
     attr(glists_kernel<T, OP>, smem);
+    attr(wide::wbatch_kernel<T, OP>, smem);
 }
 
 template <typename T>
@@ -123,6 +156,8 @@ template void lists_launch<GT, GOP>(const sfmm_ctx *, const Geometry &, cudaStre
 template void glists_launch<GT, GOP>(const sfmm_ctx *, const Geometry &, cudaStream_t, const DevTables<GT> &,
                                      const GT *const *, const GT *, const long long *, GT *const *, int, int,
                                      long long, int, int, GT *, unsigned long long *, int *);
+template bool wide_launch<GT, GOP>(const sfmm_ctx *, int, cudaStream_t, const DevTables<GT> &,
+                                   const GT *const *, GT *const *, const GT *, int, int, long long, int, int *);
 template void set_generic_attrs<GT, GOP>(size_t);
 #else
 using GT = SFMM_GENERIC_T;

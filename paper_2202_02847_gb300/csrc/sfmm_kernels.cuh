@@ -25,6 +25,15 @@ struct DevTables {
     const T *c, *ic;         // sqrt((n-m)!(n+m)!) and its inverse, n(n+1)/2+m
                              // (FP32: times 2^-n and 2^n, see row_pow2)
     const T *Tz[3];          // z-axis translation blocks per op
+    // The same matrices transposed for the warp-cooperative kernels
+    // (sfmm_wide.cuh), whose lanes each take one output and read entry i of
+    // their rows together: FT row n holds entry i of the packed F row m at
+    // i (n+1) + m (n/2+1 entries deep, zero past a row's end), GT row n entry
+    // i of the G row m >= 1 at i n + m - 1 ((n+1)/2 deep), TzT block m entry
+    // (n-m, k-m) of Tz at (k-m) (Pmax-m) + n-m.
+    const T *FT, *GT;
+    const int *FTrow, *GTrow;
+    const T *TzT[3];
     int Pmax;
 };
 
@@ -70,6 +79,8 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return f
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double sqrt_t(double a) { return sqrt(a); }
 __device__ __forceinline__ float sqrt_t(float a) { return sqrtf(a); }
+__device__ __forceinline__ double rsqrt_t(double a) { return rsqrt(a); }
+__device__ __forceinline__ float rsqrt_t(float a) { return rsqrtf(a); }
 
 template <typename T>
 __device__ __forceinline__ T ldt(const T *p) { return __ldg(p); }

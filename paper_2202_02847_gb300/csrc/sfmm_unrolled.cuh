@@ -346,18 +346,13 @@ __device__ __forceinline__ void rows_out(Sw<T> X, const Powers<T, P> &pw, T so, 
     }
 }
 
-// One row or column per step.
+// The step bodies.  Unpaired: step K < P is input row K, P <= K < 2P column
+// K - P, 2P <= K < 3P output row K - 2P.
 template <typename T, int P, int OP, int K>
-__device__ __forceinline__ void step_switch(int st, Sw<T> X, const Powers<T, P> &pw, T s, T so) {
-    if constexpr (K < 3 * P) {
-        if (st == K) {
-            if constexpr (K < P) rows_in<T, P, OP, K>(X, pw, s, T(0));
-            else if constexpr (K < 2 * P) columns_z<T, P, OP, K - P>(X);
-            else rows_out<T, P, OP, K - 2 * P>(X, pw, so, T(0));
-        } else {
-            step_switch<T, P, OP, K + 1>(st, X, pw, s, so);
-        }
-    }
+__device__ __forceinline__ void step_body(Sw<T> X, const Powers<T, P> &pw, T s, T so) {
+    if constexpr (K < P) rows_in<T, P, OP, K>(X, pw, s, T(0));
+    else if constexpr (K < 2 * P) columns_z<T, P, OP, K - P>(X);
+    else if constexpr (K < 3 * P) rows_out<T, P, OP, K - 2 * P>(X, pw, so, T(0));
 }
 
 // Paired steps: rows n and P-1-n (columns M and P-1-M) share one step, so
@@ -366,26 +361,52 @@ __device__ __forceinline__ void step_switch(int st, Sw<T> X, const Powers<T, P> 
 // Only the M2L lists kernel pairs its steps: the batch kernels and the M2M and
 // L2L lists kernels have no registers to spare for a second row and the row
 // scales of every row (they would spill).
-template <typename T, int P, int OP, int K, bool ACC = false>
-__device__ __forceinline__ void step_switch2(int st, Sw<T> X, const Powers<T, P> &pw, const T *sin,
-                                             const T *sout, TAcc acc = TAcc{0, true}) {
+template <typename T, int P, int OP, int K, bool ACC>
+__device__ __forceinline__ void step_body2(Sw<T> X, const Powers<T, P> &pw, const T *sin,
+                                           const T *sout, TAcc acc) {
     constexpr int H = (P + 1) / 2;
     if constexpr (K < 3 * H) {
-        if (st == K) {
-            constexpr int ph = K / H, i = K % H, j = P - 1 - i;
-            if constexpr (ph == 0) {
-                rows_in<T, P, OP, i>(X, pw, sin[i], T(0));
-                if constexpr (j != i) rows_in<T, P, OP, j>(X, pw, sin[j], T(0));
-            } else if constexpr (ph == 1) {
-                columns_z<T, P, OP, i>(X);
-                if constexpr (j != i) columns_z<T, P, OP, j>(X);
-            } else {
-                rows_out<T, P, OP, i, ACC>(X, pw, sout[i], T(0), acc);
-                if constexpr (j != i) rows_out<T, P, OP, j, ACC>(X, pw, sout[j], T(0), acc);
-            }
+        constexpr int ph = K / H, i = K % H, j = P - 1 - i;
+        if constexpr (ph == 0) {
+            rows_in<T, P, OP, i>(X, pw, sin[i], T(0));
+            if constexpr (j != i) rows_in<T, P, OP, j>(X, pw, sin[j], T(0));
+        } else if constexpr (ph == 1) {
+            columns_z<T, P, OP, i>(X);
+            if constexpr (j != i) columns_z<T, P, OP, j>(X);
         } else {
-            step_switch2<T, P, OP, K + 1, ACC>(st, X, pw, sin, sout, acc);
+            rows_out<T, P, OP, i, ACC>(X, pw, sout[i], T(0), acc);
+            if constexpr (j != i) rows_out<T, P, OP, j, ACC>(X, pw, sout[j], T(0), acc);
         }
+    }
+}
+
+// One row or column (or pair) per step, selected by one switch over the step
+// number (a jump table; at most 3 PC = 36 steps), not by a chain of
+// comparisons.  Cases past the last step are empty.
+#define SFMM_STEP_CASES(C)                                                                     \
+    C(0) C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8) C(9) C(10) C(11) C(12) C(13) C(14) C(15)       \
+    C(16) C(17) C(18) C(19) C(20) C(21) C(22) C(23) C(24) C(25) C(26) C(27) C(28) C(29) C(30)   \
+    C(31) C(32) C(33) C(34) C(35)
+static_assert(3 * PC <= 36, "one switch case per step");
+
+template <typename T, int P, int OP>
+__device__ __forceinline__ void step_switch(int st, Sw<T> X, const Powers<T, P> &pw, T s, T so) {
+    switch (st) {
+#define SFMM_CASE(K) case K: step_body<T, P, OP, K>(X, pw, s, so); break;
+        SFMM_STEP_CASES(SFMM_CASE)
+#undef SFMM_CASE
+        default: break;
+    }
+}
+
+template <typename T, int P, int OP, bool ACC>
+__device__ __forceinline__ void step_switch2(int st, Sw<T> X, const Powers<T, P> &pw, const T *sin,
+                                             const T *sout, TAcc acc) {
+    switch (st) {
+#define SFMM_CASE(K) case K: step_body2<T, P, OP, K, ACC>(X, pw, sin, sout, acc); break;
+        SFMM_STEP_CASES(SFMM_CASE)
+#undef SFMM_CASE
+        default: break;
     }
 }
 
@@ -393,13 +414,15 @@ __device__ __forceinline__ void step_switch2(int st, Sw<T> X, const Powers<T, P>
 // PAIRED (M2L in the lists kernel) runs two rows or columns per step.
 template <typename T, int P, int OP, bool PAIRED = false, bool ACC = false>
 __device__ __forceinline__ void translate_u(Sw<T> X, T x, T y, T z, TAcc acc = TAcc{0, true}) {
+    // |r| and rho from one reciprocal square root each (cheaper on the FP64
+    // pipe than a square root and a division).
     const T rho2 = x * x + y * y;
-    const T R = sqrt_t(rho2 + z * z);
-    if (OP != OP_M2L && !(R > T(0))) return;            // zero shift: identity
-    const T rho = sqrt_t(rho2);
-    T ca = T(1), sa = T(0);                               // cos(alpha) = y/rho, sin(alpha) = x/rho
-    if (rho > T(0)) { const T ir = T(1) / rho; ca = y * ir; sa = x * ir; }
-    const T iR = T(1) / R;
+    const T R2 = rho2 + z * z;
+    if (OP != OP_M2L && !(R2 > T(0))) return;           // zero shift: identity
+    const T iR = rsqrt_t(R2);
+    const T R = R2 * iR;
+    T ca = T(1), sa = T(0), rho = T(0);                   // cos(alpha) = y/rho, sin(alpha) = x/rho
+    if (rho2 > T(0)) { const T ir = rsqrt_t(rho2); ca = y * ir; sa = x * ir; rho = rho2 * ir; }
     const T cb = z * iR, sb = -rho * iR;                  // cos(beta) = z/|r|, sin(beta) = -rho/|r|
     Powers<T, P> pw;
     pw.ar[0] = T(1); pw.ai[0] = T(0); pw.br[0] = T(1); pw.bi[0] = T(0);
@@ -427,12 +450,12 @@ __device__ __forceinline__ void translate_u(Sw<T> X, T x, T y, T z, TAcc acc = T
 #pragma unroll
         for (int n = 1; n < P; ++n) { sin[n] = sin[n - 1] * step_in; sout[n] = sout[n - 1] * step_out; }
 #pragma unroll 1
-        for (int st = 0; st < 3 * ((P + 1) / 2); ++st) step_switch2<T, P, OP, 0, ACC>(st, X, pw, sin, sout, acc);
+        for (int st = 0; st < 3 * ((P + 1) / 2); ++st) step_switch2<T, P, OP, ACC>(st, X, pw, sin, sout, acc);
     } else {
         T s = s0, so = T(1);
 #pragma unroll 1
         for (int st = 0; st < 3 * P; ++st) {
-            step_switch<T, P, OP, 0>(st, X, pw, s, so);
+            step_switch<T, P, OP>(st, X, pw, s, so);
             if (st < P) s *= step_in;
             else if (st >= 2 * P) so *= step_out;
         }

@@ -106,12 +106,20 @@ class TranslationServer:
         self.device = torch.device(device)
         self.P_max = P_max
         self.streams = [torch.cuda.Stream(self.device) for _ in range(n_streams)]
+        # Two streams of the highest priority: `fast` runs the requests whose
+        # remaining work fits in one chunk, so that a small request does not
+        # queue behind the chunks of large ones (its blocks are scheduled
+        # before theirs as SMs free up), and `prep` runs the marshalling of
+        # newly admitted requests (a few small kernels each).
+        self.fast = torch.cuda.Stream(self.device, priority=-100)
+        self.prep = torch.cuda.Stream(self.device, priority=-100)
+        lanes = self.streams + [self.fast]
         # one handle per stream and dtype: launches that use a handle's global
         # scratch run one after another, so streams with their own handles overlap
-        self.hs = {"f64": [sfmm.Handle(P_max, "f64") for _ in self.streams],
-                   "f32": [sfmm.Handle(P_max, "f32") for _ in self.streams]}
+        self.hs = {"f64": [sfmm.Handle(P_max, "f64") for _ in lanes],
+                   "f32": [sfmm.Handle(P_max, "f32") for _ in lanes]}
         self.h = {k: v[0] for k, v in self.hs.items()}
-        self._sidx = {id(s): i for i, s in enumerate(self.streams)}
+        self._sidx = {id(s): i for i, s in enumerate(lanes)}
         self.chunk = chunk                   # most translations in one chunk
         self.chunk_flop = chunk_flop         # target work of one chunk
         self.age_limit_s = age_limit_s       # ageing bound of admission and dealing
@@ -237,7 +245,9 @@ class TranslationServer:
         pending = list(reqs)[::-1]     # not yet arrived (pop from the end)
         queue = []                     # arrived, waiting for memory
         active = []                    # admitted, chunks left to launch
-        inflight = {i: [] for i in range(len(self.streams))}   # stream -> [(ev, req)]
+        lanes = self.streams + [self.fast]
+        FAST = len(self.streams)
+        inflight = {i: [] for i in range(len(lanes))}          # stream -> [(ev, req)]
         finished = []
         while pending or queue or active or any(inflight.values()):
             now = time.perf_counter() - t0
@@ -249,7 +259,7 @@ class TranslationServer:
                 r = queue[i]
                 if self._admit(r):
                     queue.pop(i)
-                    self._prepare(r, self.streams[r.rid % len(self.streams)])
+                    self._prepare(r, self.prep)
                     r._left = self._work(r)
                     active.append(r)
                     continue
@@ -277,8 +287,17 @@ class TranslationServer:
                     else:
                         keep.append((ev, r))
                 inflight[si] = keep
-            # deal chunks onto free stream slots
+            # deal chunks onto free stream slots: first the fast stream (the
+            # request with the least remaining work, if that fits in one chunk)
             launched = False
+            if active and len(inflight[FAST]) < self.inflight:
+                r = min(active, key=lambda x: (x._left, x.arrival))
+                if r._left <= self.chunk_flop:
+                    ev = self._launch_chunk(r, self.fast)
+                    inflight[FAST].append((ev, r))
+                    if r._next >= r.count:
+                        active.remove(r)
+                    launched = True
             for si, s in enumerate(self.streams):
                 if len(inflight[si]) >= self.inflight or not active:
                     continue
@@ -341,14 +360,23 @@ def poisson_arrivals(requests, rate_per_s, seed=55):
     return requests
 
 
-def latency_stats(finished):
+def latency_stats(finished, alone_ms=None):
     """Latency percentiles (host clock, arrival to completion), and the
-    percentiles of latency per GFLOP of the request's work (a slowdown
-    measure: the workload's service times span five orders of magnitude)."""
+    percentiles of latency per GFLOP of the request's work.  The workload's
+    service times span five orders of magnitude (counts 1e3..1e6 times a
+    per-translation cost that grows as P^3), so the latency percentiles mostly
+    rank request sizes; `alone_ms` (request id -> latency of the same request
+    served alone on an idle device) adds the slowdown percentiles, latency in
+    the mix over latency alone, which compare each request with itself."""
     lat = np.array([r.done_ms - 1e3 * r.arrival for r in finished])
     work = np.array([translation_flop(r.p_in, r.p_out) * r.count for r in finished]) * 1e-9
     per = lat / work
-    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "n": len(lat),
-            "p50_ms_per_gflop": float(np.percentile(per, 50)),
-            "p99_ms_per_gflop": float(np.percentile(per, 99))}
+    st = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+          "mean_ms": float(lat.mean()), "n": len(lat),
+          "p50_ms_per_gflop": float(np.percentile(per, 50)),
+          "p99_ms_per_gflop": float(np.percentile(per, 99))}
+    if alone_ms:
+        slow = np.array([(r.done_ms - 1e3 * r.arrival) / max(alone_ms[r.rid], 1e-3) for r in finished])
+        st["p50_slowdown"] = float(np.percentile(slow, 50))
+        st["p99_slowdown"] = float(np.percentile(slow, 99))
+    return st

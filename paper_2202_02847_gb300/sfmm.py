@@ -187,7 +187,7 @@ class ListClass(ctypes.Structure):
 
 
 MAX_CLASSES = 256
-POLICY = {"auto": 0, "unrolled": 1, "shared": 2, "global": 3}
+POLICY = {"auto": 0, "unrolled": 1, "shared": 2, "global": 3, "wide": 4}
 
 
 def translate_lists_multi(h, classes, src, shift, offsets, out, accumulate=False, stream=None):
