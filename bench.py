@@ -849,9 +849,13 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the per-order sweep and the other configurations' summaries "
                          "that the default single-GPU run appends to its line")
-    ap.add_argument("--config", default="octree", choices=["octree", "serving", "batching", "precision"],
+    ap.add_argument("--config", default="octree",
+                    choices=["octree", "serving", "batching", "precision", "per-order"],
                     help="octree: the FP64 P=10 octree pass (default); serving: the request "
-                         "loop; batching: the mixed-order adaptive-octree pass")
+                         "loop; batching: the mixed-order adaptive-octree pass; per-order: the "
+                         "M2L batch sweep over orders (--orders, --dtype)")
+    ap.add_argument("--orders", default="4,6,8,10,12,16,20,24,30",
+                    help="per-order: comma-separated orders")
     ap.add_argument("--points", type=int, default=1 << 21, help="batching: Plummer points")
     ap.add_argument("--autotune", action="store_true",
                     help="batching: autotune the policies of the separate-launch pass shown beside it")
@@ -865,6 +869,12 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.config == "per-order":
+        import __graft_entry__
+        __graft_entry__.build_library()
+        orders = [int(x) for x in args.orders.split(",")]
+        print(json.dumps(per_order_sweep(orders, args.dtype)))
         return
     if args.config in ("serving", "batching", "precision"):
         print(json.dumps({"serving": run_serving, "batching": run_batching,
