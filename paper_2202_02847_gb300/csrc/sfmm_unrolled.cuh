@@ -467,25 +467,28 @@ __device__ __forceinline__ void translate_u(Sw<T> X, T x, T y, T z, TAcc acc = T
 // is an asynchronous global-to-shared copy (cp.async), so all of a round's
 // loads are in flight together and the warp waits once, instead of once per
 // batch of loads held in registers; the caller's __syncwarp() then publishes
-// the copies to the whole warp.
+// the copies to the whole warp.  A null solid is copied with a source size of
+// zero, which fills the destination with zeros and reads nothing (the source
+// address is then `dummy`, any readable global address), so the copies need
+// no branch on the pointer.
 template <typename T>
-__device__ __forceinline__ void copy_async(T *dst, const T *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;"
-                 :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src), "n"((int)sizeof(T)) : "memory");
+__device__ __forceinline__ void copy_async(T *dst, const T *src, uint32_t nbytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;"
+                 :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src), "n"((int)sizeof(T)), "r"(nbytes)
+                 : "memory");
 }
 template <typename T, int S>
-__device__ __forceinline__ void load_solids(Sw<T> X, const T *mine) {
+__device__ __forceinline__ void load_solids(Sw<T> X, const T *mine, const void *dummy) {
 #pragma unroll 4
     for (int j = 0; j < 32; ++j) {
         const T *p = reinterpret_cast<const T *>(
             __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(mine), j));
+        const uint32_t nb = p ? (uint32_t)sizeof(T) : 0u;
+        const T *q = p ? p : reinterpret_cast<const T *>(dummy);
 #pragma unroll
         for (int e0 = 0; e0 < S; e0 += 32) {
             const int e = e0 + X.lane;
-            if (e < S) {
-                if (p) copy_async(&X.at(e, j), p + e);
-                else X.at(e, j) = T(0);
-            }
+            if (e < S) copy_async(&X.at(e, j), p ? q + e : q, nb);
         }
     }
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
@@ -510,7 +513,7 @@ __global__ void __launch_bounds__(256, 1) ubatch_kernel(const T *const *in, T *c
             src = nullptr;
             dst = nullptr;
         }
-        load_solids<T, S>(X, src);
+        load_solids<T, S>(X, src, in);
         __syncwarp();
         T x = T(0), y = T(0), z = T(1);
         if (src) { x = shift[3 * i]; y = shift[3 * i + 1]; z = shift[3 * i + 2]; }
@@ -572,7 +575,7 @@ __global__ void __launch_bounds__(256, 1) ulists_kernel(const T *const *src, con
             const long long j = j0 + (long long)r * G + mem;
             const T *s = (j < j1) ? src[j] : nullptr;
             if (j < j1 && s == nullptr) atomicOr(status, STATUS_NULL_POINTER);
-            load_solids<T, S>(X, s);
+            load_solids<T, S>(X, s, src);
             __syncwarp();
             T x = T(0), y = T(0), z = T(1);
             if (s) { x = shift[3 * j]; y = shift[3 * j + 1]; z = shift[3 * j + 2]; }
@@ -661,7 +664,7 @@ __global__ void __launch_bounds__(256, 1) ulists_acc_kernel(const T *const *src,
             const long long j = j0 + (long long)r * 32 + lane;
             const T *s = (j < j1) ? src[j] : nullptr;
             if (j < j1 && s == nullptr) atomicOr(status, STATUS_NULL_POINTER);
-            load_solids<T, S>(X, s);
+            load_solids<T, S>(X, s, src);
             __syncwarp();
             T x = T(0), y = T(0), z = T(1);
             if (s) { x = shift[3 * j]; y = shift[3 * j + 1]; z = shift[3 * j + 2]; }
