@@ -427,12 +427,26 @@ __device__ __forceinline__ void translate_u(Sw<T> X, T x, T y, T z, TAcc acc = T
     Powers<T, P> pw;
     pw.ar[0] = T(1); pw.ai[0] = T(0); pw.br[0] = T(1); pw.bi[0] = T(0);
     if constexpr (P > 1) { pw.ar[1] = ca; pw.ai[1] = sa; pw.br[1] = cb; pw.bi[1] = sb; }
+    if constexpr (sizeof(T) == 8) {
+        // FP64: the three-term recurrence X_m = 2 cos(theta) X_{m-1} - X_{m-2} for
+        // both components, one FMA each instead of a complex multiplication
+        // (rounding below 1e-14 for m < 12)
+        const T ta = T(2) * ca, tb = T(2) * cb;
 #pragma unroll
-    for (int m = 2; m < P; ++m) {
-        pw.ar[m] = pw.ar[m - 1] * ca - pw.ai[m - 1] * sa;
-        pw.ai[m] = fma_t(pw.ar[m - 1], sa, pw.ai[m - 1] * ca);
-        pw.br[m] = pw.br[m - 1] * cb - pw.bi[m - 1] * sb;
-        pw.bi[m] = fma_t(pw.br[m - 1], sb, pw.bi[m - 1] * cb);
+        for (int m = 2; m < P; ++m) {
+            pw.ar[m] = fma_t(ta, pw.ar[m - 1], -pw.ar[m - 2]);
+            pw.ai[m] = fma_t(ta, pw.ai[m - 1], -pw.ai[m - 2]);
+            pw.br[m] = fma_t(tb, pw.br[m - 1], -pw.br[m - 2]);
+            pw.bi[m] = fma_t(tb, pw.bi[m - 1], -pw.bi[m - 2]);
+        }
+    } else {
+#pragma unroll
+        for (int m = 2; m < P; ++m) {
+            pw.ar[m] = pw.ar[m - 1] * ca - pw.ai[m - 1] * sa;
+            pw.ai[m] = fma_t(pw.ar[m - 1], sa, pw.ai[m - 1] * ca);
+            pw.br[m] = pw.br[m - 1] * cb - pw.bi[m - 1] * sb;
+            pw.bi[m] = fma_t(pw.br[m - 1], sb, pw.bi[m - 1] * cb);
+        }
     }
     // Row scales: input |r|^{-(n+1)} (M2L), |r|^{-n} (M2M), |r|^{n} (L2L);
     // output |r|^{-n} (M2L, L2L), |r|^{n} (M2M).
@@ -478,18 +492,29 @@ __device__ __forceinline__ void copy_async(T *dst, const T *src, uint32_t nbytes
                  : "memory");
 }
 template <typename T, int S>
-__device__ __forceinline__ void load_solids(Sw<T> X, const T *mine, const void *dummy) {
-#pragma unroll 4
-    for (int j = 0; j < 32; ++j) {
-        const T *p = reinterpret_cast<const T *>(
-            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(mine), j));
-        const uint32_t nb = p ? (uint32_t)sizeof(T) : 0u;
-        const T *q = p ? p : reinterpret_cast<const T *>(dummy);
+__device__ __forceinline__ void copy_solid(Sw<T> X, const T *mine, const void *dummy, int j) {
+    const T *p = reinterpret_cast<const T *>(
+        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(mine), j));
+    const uint32_t nb = p ? (uint32_t)sizeof(T) : 0u;
+    const T *q = p ? p : reinterpret_cast<const T *>(dummy);
 #pragma unroll
-        for (int e0 = 0; e0 < S; e0 += 32) {
-            const int e = e0 + X.lane;
-            if (e < S) copy_async(&X.at(e, j), p ? q + e : q, nb);
-        }
+    for (int e0 = 0; e0 < S; e0 += 32) {
+        const int e = e0 + X.lane;
+        if (e < S) copy_async(&X.at(e, j), p ? q + e : q, nb);
+    }
+}
+// The loop over the 32 solids is unrolled fully in FP64 and four times in FP32
+// (measured: full unrolling gains 0.5 % on the FP64 octree pass and loses
+// 1.5 % on the FP32 one, whose larger number of resident warps at different
+// steps already strains the instruction cache).
+template <typename T, int S>
+__device__ __forceinline__ void load_solids(Sw<T> X, const T *mine, const void *dummy) {
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) copy_solid<T, S>(X, mine, dummy, j);
+    } else {
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) copy_solid<T, S>(X, mine, dummy, j);
     }
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
