@@ -535,7 +535,8 @@ def run_serving(args):
     __graft_entry__.build_library()
     from paper_2202_02847_gb300 import serve
     srv = serve.TranslationServer(P_max=30, pool_size=4096, n_shifts=1 << 20,
-                                  arena_bytes=24 << 30, n_streams=4)
+                                  arena_bytes=24 << 30, n_streams=4,
+                                  chunk_flop=getattr(args, "chunk_flop", 1e9))
     # warm-up: one small request of every kind that the mix uses
     warm = serve.make_requests(24, seed=99, count_lo=1e3, count_hi=2e3)
     srv.run(warm)
@@ -575,7 +576,8 @@ def run_serving(args):
                                "(10% p_out = p_in +- U{1..4}), counts log-uniform 1e3..1e6, "
                                "FP32/FP64, |r|/box in [2,4], resident pools",
                    "requests_per_load_point": len(reqs), "streams": 4,
-                   "chunk": "about 1e9 FLOP of translations, at least a quarter wave of the batch kernel",
+                   "chunk": f"about {getattr(args, 'chunk_flop', 1e9):.2g} FLOP of translations, "
+                            "at least a quarter wave of the batch kernel",
                    "scheduling": "first-fit admission and shortest-remaining-work dealing, "
                                  "both with a 0.25 s ageing bound; requests whose remaining work "
                                  "fits one chunk on a fifth stream of high priority, marshalling "
@@ -860,6 +862,8 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="batching: autotune the policies of the separate-launch pass shown beside it")
     ap.add_argument("--requests", type=int, default=600, help="serving: requests per load point")
+    ap.add_argument("--chunk-flop", type=float, default=1e9,
+                    help="serving: target work of one chunk (FLOP)")
     ap.add_argument("--extras-requests", type=int, default=240,
                     help="serving requests per load point in the default run's summary")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"],
