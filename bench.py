@@ -595,6 +595,32 @@ def run_serving(args):
 
 
 
+def ncu_profiles():
+    """The ncu counters of every committed profile summary (`counter.<name>:
+    <value>` lines of profiles/*.md), per file: the per-kernel evidence behind
+    each configuration's numbers, attached to the JSON line.  Values are as
+    captured (each file gives its command and workload); the headline kernel's
+    DRAM traffic enters `roofline.traffic` only while its sources are the ones
+    captured (ncu_traffic)."""
+    import glob
+    import re
+    out = {}
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        kv = {}
+        for line in open(path):
+            m = re.match(r"\s*counter\.([\w.]+):\s*(.*?)\s*$", line)
+            if m:
+                v = m.group(2)
+                try:
+                    v = float(v) if any(c in v for c in ".e") else int(v)
+                except ValueError:
+                    pass
+                kv[m.group(1)] = v
+        if kv:
+            out[os.path.basename(path)] = kv
+    return out
+
+
 def hbm_peak():
     """Measured HBM copy bandwidth in GB/s (MEASURED_PEAKS.json), else the
     6,800 GB/s of an earlier GB300 measurement."""
@@ -1017,6 +1043,7 @@ def main():
     if rank == 0 and world == 1 and depth == DEPTH and args.dtype == "f64" and not args.no_extras:
         line.update(run_extras(args))
     if rank == 0:
+        line["ncu_profiles"] = ncu_profiles()
         print(json.dumps(line))
     h.close()
     if dist is not None:

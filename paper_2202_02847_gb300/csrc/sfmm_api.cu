@@ -466,6 +466,7 @@ const char *sfmm_status_string(sfmm_status s) {
 }
 
 sfmm_status sfmm_create(int P_max, sfmm_dtype dtype, sfmm_handle *out) {
+    SfmmRange nvtx_range("sfmm_create");
     if (out == nullptr) return SFMM_ERR_ARG;
     *out = nullptr;
     if (dtype != SFMM_F64 && dtype != SFMM_F32) return SFMM_ERR_ARG;
@@ -556,18 +557,21 @@ sfmm_status sfmm_get_info(sfmm_handle h, int *P_max, sfmm_dtype *dtype) {
 sfmm_status sfmm_m2m_batch(sfmm_handle h, const void *const *in, void *const *out,
                            const void *shift, int p_in, int p_out, long long count,
                            int accumulate, sfmm_stream stream) {
+    SfmmRange nvtx_range("sfmm_m2m_batch");
     return batch(h, OP_M2M, in, out, shift, p_in, p_out, count, accumulate, stream);
 }
 
 sfmm_status sfmm_m2l_batch(sfmm_handle h, const void *const *in, void *const *out,
                            const void *shift, int p_in, int p_out, long long count,
                            int accumulate, sfmm_stream stream) {
+    SfmmRange nvtx_range("sfmm_m2l_batch");
     return batch(h, OP_M2L, in, out, shift, p_in, p_out, count, accumulate, stream);
 }
 
 sfmm_status sfmm_l2l_batch(sfmm_handle h, const void *const *in, void *const *out,
                            const void *shift, int p_in, int p_out, long long count,
                            int accumulate, sfmm_stream stream) {
+    SfmmRange nvtx_range("sfmm_l2l_batch");
     return batch(h, OP_L2L, in, out, shift, p_in, p_out, count, accumulate, stream);
 }
 
@@ -575,6 +579,7 @@ sfmm_status sfmm_translate_lists(sfmm_handle h, sfmm_op op, const void *const *s
                                  const void *shift, const long long *offsets,
                                  void *const *out, int p_in, int p_out,
                                  long long n_targets, int accumulate, sfmm_stream stream) {
+    SfmmRange nvtx_range("sfmm_translate_lists");
     sfmm_status st = check_common(h, p_in, p_out, n_targets);
     if (st != SFMM_OK) return st;
     if (op != SFMM_M2M && op != SFMM_M2L && op != SFMM_L2L) return SFMM_ERR_ARG;
@@ -606,12 +611,14 @@ static sfmm_status p2x(sfmm_handle h, bool singular, int P, const void *points, 
 sfmm_status sfmm_p2m_boxes(sfmm_handle h, int P, const void *points, const void *q,
                            const long long *offsets, const void *centres, void *out,
                            long long n_boxes, sfmm_stream stream) {
+    SfmmRange nvtx_range("sfmm_p2m_boxes");
     return p2x(h, false, P, points, q, offsets, centres, out, n_boxes, stream);
 }
 
 sfmm_status sfmm_p2l_boxes(sfmm_handle h, int P, const void *points, const void *q,
                            const long long *offsets, const void *centres, void *out,
                            long long n_boxes, sfmm_stream stream) {
+    SfmmRange nvtx_range("sfmm_p2l_boxes");
     return p2x(h, true, P, points, q, offsets, centres, out, n_boxes, stream);
 }
 
@@ -807,6 +814,7 @@ extern "C" {
 
 sfmm_status sfmm_translate_pass(sfmm_handle h, const sfmm_pass_class *classes, int n_classes,
                                 sfmm_stream stream) {
+    SfmmRange nvtx_range("sfmm_translate_pass");
     if (h == nullptr || classes == nullptr || n_classes < 1 || n_classes > SFMM_MAX_PASS_CLASSES)
         return SFMM_ERR_ARG;
     for (int k = 0; k < n_classes; ++k) {
@@ -832,6 +840,7 @@ sfmm_status sfmm_translate_lists_multi(sfmm_handle h, const sfmm_list_class *cla
                                        int n_classes, const void *const *src,
                                        const void *shift, const long long *offsets,
                                        void *const *out, int accumulate, sfmm_stream stream) {
+    SfmmRange nvtx_range("sfmm_translate_lists_multi");
     if (h == nullptr || classes == nullptr || n_classes < 1 || n_classes > SFMM_MAX_CLASSES)
         return SFMM_ERR_ARG;
     for (int k = 0; k < n_classes; ++k) {

@@ -6,8 +6,20 @@
 #include <cstddef>
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sfmm.h"
 #include "sfmm_kernels.cuh"
+
+// An NVTX range named after the API call, open for the call's duration (its
+// launches and host work), so that a timeline tool shows every entry point;
+// a no-op unless such a tool is attached.
+struct SfmmRange {
+    explicit SfmmRange(const char *name) { nvtxRangePushA(name); }
+    ~SfmmRange() { nvtxRangePop(); }
+    SfmmRange(const SfmmRange &) = delete;
+    SfmmRange &operator=(const SfmmRange &) = delete;
+};
 
 struct sfmm_ctx {
     int Pmax = 0;

@@ -699,6 +699,7 @@ bool encode_source_map(EncodeTiled enc, CUtensorMap *m, __half *base, int nside,
 extern "C" {
 
 sfmm_status sfmm_grid_create(sfmm_handle h, int P, int nside, sfmm_grid *out) {
+    SfmmRange nvtx_range("sfmm_grid_create");
     if (out == nullptr || h == nullptr) return SFMM_ERR_ARG;
     *out = nullptr;
     if (P != GP) return SFMM_ERR_UNSUPPORTED;
@@ -881,6 +882,7 @@ sfmm_status sfmm_grid_inject_timeout(sfmm_grid g, long long after_chunks) {
 
 sfmm_status sfmm_grid_m2l(sfmm_grid g, double box_size, const void *M, void *L, int accumulate,
                           sfmm_stream stream) {
+    SfmmRange nvtx_range("sfmm_grid_m2l");
     if (g == nullptr || M == nullptr || L == nullptr || !(box_size > 0)) return SFMM_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int ns = g->nside;
