@@ -150,6 +150,26 @@ def translation_cost(p_in, p_out):
     return p_in * (p_in + 1) * (2 * p_in + 1) // 6 + p_out * (p_out + 1) * (2 * p_out + 1) // 6 + z
 
 
+def coarsen_lanes(classes, min_lanes):
+    """A wave's classes (op, p_in, p_out, first row, end row, lanes) with at
+    least `min_lanes` lanes per target: runs of adjacent rows of one order pair
+    that end up with the same lanes are merged into one class.  Rows of one
+    order pair are sorted by decreasing list length, so a merged class still
+    gives every list at least as many lanes as its length needs (up to 32).
+    The merged classes keep the order of the input (most expensive first
+    chunk first), each at the place of its earliest part."""
+    rank = {c[3]: k for k, c in enumerate(classes)}     # row ranges are disjoint
+    out = []
+    for c in sorted(classes, key=lambda c: (c[1], c[2], c[3])):
+        g = max(c[5], min_lanes)
+        if out and out[-1][0][1:3] == c[1:3] and out[-1][0][4] == c[3] and out[-1][0][5] == g:
+            m, r = out[-1]
+            out[-1] = ((m[0], m[1], m[2], m[3], c[4], g), min(r, rank[c[3]]))
+        else:
+            out.append(((c[0], c[1], c[2], c[3], c[4], g), rank[c[3]]))
+    return [c for c, _ in sorted(out, key=lambda x: x[1])]
+
+
 def lanes_for_length(lengths):
     """Lanes per target for lists of the given lengths: the smallest power of
     two >= the length, capped at 32 (one warp); 1 for lists of 0 or 1 source.
@@ -338,15 +358,24 @@ class AdaptivePass:
         self.m2l_all(stream)
         self.downward(stream)
 
-    def pass_plan(self, parts=("m2m", "m2l", "l2l")):
+    def pass_plan(self, parts=("m2m", "m2l", "l2l"), min_lanes=1):
         """The pass as phased classes for sfmm_translate_pass: one phase per M2M
         level (deepest first, parents overwritten), one per M2L wave (the
         wave's classes, accumulating), one per L2L level (each child a list of
         its parent, accumulating).  Built once per choice of parts; the
         arrays it points into are held by the pass object."""
-        key = tuple(parts)
+        key = (tuple(parts), min_lanes)
         if key in self._plans:
             return self._plans[key]
+        # a launch takes at most MAX_PASS_CLASSES classes: raise the fewest lanes
+        # per target until the M2L waves' lane classes fit (merged ranges run
+        # their shorter lists with idle lanes; the sums are unchanged)
+        fixed = (len(self.m2m) if "m2m" in parts else 0) + (len(self.l2l) if "l2l" in parts else 0)
+        waves = [coarsen_lanes(d["classes"], min_lanes) for d in self.waves]
+        while "m2l" in parts and fixed + sum(len(c) for c in waves) > sfmm.MAX_PASS_CLASSES \
+                and min_lanes < 32:
+            min_lanes *= 2
+            waves = [coarsen_lanes(d["classes"], min_lanes) for d in self.waves]
         cls, keep, ph = [], [], 0
         if "m2m" in parts:
             for d in self.m2m:
@@ -354,8 +383,8 @@ class AdaptivePass:
                             d["offsets"], d["out"]))
                 ph += 1
         if "m2l" in parts:
-            for d in self.waves:
-                for op, pi, po, tb, te, g in d["classes"]:
+            for d, wcls in zip(self.waves, waves):
+                for op, pi, po, tb, te, g in wcls:
                     cls.append((op, pi, po, g, ph, True, te - tb, d["src"], d["shift"],
                                 d["offsets"][tb:], d["out"][tb:]))
                 ph += 1
@@ -370,14 +399,16 @@ class AdaptivePass:
         self._plans[key] = plan
         return plan
 
-    def run_pass(self, parts=("m2m", "m2l", "l2l"), stream=None):
+    def run_pass(self, parts=("m2m", "m2l", "l2l"), stream=None, min_lanes=1):
         """The chosen parts of the pass as one persistent launch."""
-        sfmm.translate_pass(self.h, self.pass_plan(parts)[0], stream=stream)
+        sfmm.translate_pass(self.h, self.pass_plan(parts, min_lanes)[0], stream=stream)
 
-    def step_one_launch(self, stream=None):
-        """The whole pass (locals zeroed first) as one persistent launch."""
+    def step_one_launch(self, stream=None, min_lanes=1):
+        """The whole pass (locals zeroed first) as one persistent launch;
+        min_lanes > 1 runs every list with at least that many lanes (the form a
+        pass takes when its lane classes exceed the launch's class limit)."""
         self.L.zero_()
-        self.run_pass(stream=stream)
+        self.run_pass(stream=stream, min_lanes=min_lanes)
 
     def launches_per_step(self):
         m2l = sum((len(d["classes"]) + sfmm.MAX_CLASSES - 1) // sfmm.MAX_CLASSES if d["fused"]

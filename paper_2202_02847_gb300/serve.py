@@ -50,6 +50,7 @@ class Request:
     done_ms: float = None
     out: torch.Tensor = None
     chunks_left: int = 0
+    rejected: str = None     # why the request was not served (None: served)
 
     def out_bytes(self):
         w = 8 if self.dtype == "f64" else 4
@@ -67,6 +68,7 @@ class Arena:
 
     def __init__(self, nbytes, device):
         self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.size = nbytes
         self.free = [(0, nbytes)]          # sorted (offset, size)
 
     @staticmethod
@@ -153,11 +155,32 @@ class TranslationServer:
         torch.cuda.synchronize(self.device)
 
     # ----------------------------------------------------------- admission
+    @staticmethod
+    def _need(r):
+        """Arena bytes of a request: output, two pointer arrays, shifts."""
+        w = 8 if r.dtype == "f64" else 4
+        S_out = r.p_out * (r.p_out + 1)
+        return [r.count * S_out * w, r.count * 8, r.count * 8, r.count * 3 * w]
+
+    def _reject_reason(self, r):
+        """Why a request can never be served (None if it can): an unknown op or
+        dtype, orders outside 1..P_max, no translations, or buffers larger than
+        the whole arena (it would wait for memory forever)."""
+        if r.op not in OPS or r.dtype not in ("f32", "f64"):
+            return f"unknown op or dtype ({r.op}, {r.dtype})"
+        if not (1 <= r.p_in <= self.P_max and 1 <= r.p_out <= self.P_max):
+            return f"orders {r.p_in}->{r.p_out} outside 1..{self.P_max}"
+        if r.count < 1:
+            return "no translations"
+        need = sum(Arena._round(n) for n in self._need(r))
+        if need > self.arena.size:
+            return f"needs {need} bytes of the {self.arena.size}-byte arena"
+        return None
+
     def _admit(self, r):
         """Reserve arena space for the request's output, pointers and shifts."""
         w = 8 if r.dtype == "f64" else 4
-        S_out = r.p_out * (r.p_out + 1)
-        need = [r.count * S_out * w, r.count * 8, r.count * 8, r.count * 3 * w]
+        need = self._need(r)
         got = []
         for n in need:
             a = self.arena.alloc(n)
@@ -237,8 +260,11 @@ class TranslationServer:
         request older than `age_limit_s` goes first.  Arrival and completion are
         both taken on the host clock: done_ms = when the host loop saw the
         request's last chunk complete, in ms after the start of the run.
-        Returns the finished requests; with keep_outputs the results are copied
-        out of the arena before its space is reused."""
+        A request that can never be served (orders outside 1..P_max, no
+        translations, buffers larger than the whole arena) is answered at its
+        arrival with `rejected` set and no output, and queues nothing.
+        Returns the finished requests, rejected ones included; with keep_outputs
+        the results are copied out of the arena before its space is reused."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         torch.cuda.synchronize(self.device)
         t0 = time.perf_counter()
@@ -252,7 +278,15 @@ class TranslationServer:
         while pending or queue or active or any(inflight.values()):
             now = time.perf_counter() - t0
             while pending and pending[-1].arrival <= now:
-                queue.append(pending.pop())
+                r = pending.pop()
+                why = self._reject_reason(r)
+                if why is None:
+                    queue.append(r)
+                else:                      # answered at once, never queued
+                    r.rejected = why
+                    r.done_ms = 1e3 * (time.perf_counter() - t0)
+                    r.out = None
+                    finished.append(r)
             # admission: first fit, bounded by age
             i = 0
             while i < len(queue):
@@ -368,6 +402,7 @@ def latency_stats(finished, alone_ms=None):
     rank request sizes; `alone_ms` (request id -> latency of the same request
     served alone on an idle device) adds the slowdown percentiles, latency in
     the mix over latency alone, which compare each request with itself."""
+    finished = [r for r in finished if r.rejected is None]
     lat = np.array([r.done_ms - 1e3 * r.arrival for r in finished])
     work = np.array([translation_flop(r.p_in, r.p_out) * r.count for r in finished]) * 1e-9
     per = lat / work

@@ -53,3 +53,47 @@ def test_classes_partition_rows_with_uniform_orders_and_lanes(plan):
         assert np.all(covered == 1)                               # classes partition the rows
         assert cost == sorted(cost, reverse=True)                 # costliest first chunk first
         assert len(d["classes"]) <= 256
+
+
+@pytest.mark.parametrize("min_lanes", [1, 2, 4, 8, 16, 32])
+def test_coarsened_lane_classes_still_partition_rows(plan, min_lanes):
+    """coarsen_lanes (used when a one-launch pass would exceed the launch's
+    class limit): the merged classes still partition every wave's rows, keep
+    one order pair each, give every list at least the lanes its length needs
+    and at least min_lanes, and never add classes."""
+    from paper_2202_02847_gb300.fmm import coarsen_lanes, lanes_for_length
+    tree, P, _, ap = plan
+    P = np.asarray(P)
+    for d in ap.waves:
+        h = d["host"]
+        lens = np.diff(h["offs"])
+        cc = coarsen_lanes(d["classes"], min_lanes)
+        assert len(cc) <= len(d["classes"])
+        covered = np.zeros(len(lens), int)
+        for op, pi, po, tb, te, lanes in cc:
+            covered[tb:te] += 1
+            assert lanes >= min_lanes and np.all(lanes_for_length(lens[tb:te]) <= lanes)
+            for r in range(tb, te):
+                assert np.all(P[h["src"][h["offs"][r]:h["offs"][r + 1]]] == pi)
+                assert P[h["row_tgt"][r]] == po
+        assert np.all(covered == 1)
+    if min_lanes == 1:
+        assert all(coarsen_lanes(d["classes"], 1) == d["classes"] for d in ap.waves)
+
+
+def test_pass_plan_fits_the_class_limit():
+    """A tree whose waves hold more lane classes than one pass launch takes
+    (262,144-point Plummer sphere: 389) gets a plan within the limit."""
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_2202_02847_gb300 import sfmm
+    from paper_2202_02847_gb300.fmm import AdaptivePass
+    pts, q = W.plummer(262144, seed=4)
+    tree = W.adaptive_octree(pts, leaf_size=64)
+    P = W.order_by_level(tree, lo=4, span=20)
+    ap = AdaptivePass(tree, P, None, device="cpu")
+    assert sum(len(d["classes"]) for d in ap.waves) + len(ap.m2m) + len(ap.l2l) > sfmm.MAX_PASS_CLASSES
+    cls, _, phases = ap.pass_plan()
+    assert len(cls) <= sfmm.MAX_PASS_CLASSES and phases <= 64
+    assert sum(c.n_targets for c in cls if c.op == sfmm.OPS["m2l"]) == \
+        sum(d["n"] for d in ap.waves)

@@ -185,6 +185,23 @@ def test_one_launch_pass_matches_the_multi_launch_pass(setup):
     assert torch.equal(ap.L, one)
 
 
+@pytest.mark.parametrize("min_lanes", [4, 32])
+def test_one_launch_pass_with_coarsened_lane_classes(setup, min_lanes):
+    """The one-launch pass with every list on at least min_lanes lanes (the
+    merged classes a pass gets when its lane classes exceed the class limit)
+    agrees with the separate-launch pass for every expansion within 1e-12."""
+    import torch
+    sfmm, ap, pts, q, tree, P_node, h = setup
+    ap.step()
+    torch.cuda.synchronize()
+    refL, refM = ap.L.cpu().numpy(), ap.M.cpu().numpy()
+    ap.step_one_launch(min_lanes=min_lanes)
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    _check_all_nodes(ap, tree, P_node, ap.L.cpu().numpy(), refL, "L", 1e-12,
+                     f"L after the one-launch pass, lanes >= {min_lanes}")
+
+
 def test_pass_rejects_bad_classes(setup):
     import torch
     sfmm, ap, pts, q, tree, P_node, h = setup

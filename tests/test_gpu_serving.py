@@ -67,3 +67,22 @@ def test_served_results_match_oracle(server, orc):
         tol = 1e-12 if r.dtype == "f64" else 1e-5
         U.check_rows(got, want, r.p_out, U.out_kind(r.op), tol, a=U.out_radius(r.op, sh),
                      what=f"request {r.rid} {r.op} {r.dtype} {r.p_in}->{r.p_out}")
+
+
+def test_requests_that_can_never_be_served_are_rejected(server):
+    """A request larger than the whole arena, or with an order above P_max,
+    is answered at arrival with a reason and no output (instead of waiting
+    for memory forever); the others in the same run are served."""
+    from dataclasses import replace
+    reqs = _mix()[:4]
+    big = replace(reqs[0], rid=100, op="m2l", dtype="f64", p_in=30, p_out=30, count=1_000_000)
+    high = replace(reqs[1], rid=101, p_in=31, p_out=31)
+    done = server.run(reqs + [big, high])
+    by = {r.rid: r for r in done}
+    assert len(done) == 6
+    assert by[100].rejected and "arena" in by[100].rejected and by[100].out is None
+    assert by[101].rejected and "outside" in by[101].rejected
+    for r in reqs:
+        assert by[r.rid].rejected is None and by[r.rid].done_ms is not None
+    from paper_2202_02847_gb300.serve import latency_stats
+    assert latency_stats(done)["n"] == 4
