@@ -646,21 +646,76 @@ __device__ __forceinline__ void flush_rows(Sw<T> X, uint32_t ta) {
     }
 }
 
-// FP64 M2L interaction lists, one target per warp, with each lane's running sum
-// of its translations kept in tensor memory (free in this kernel: 256 KB per
-// SM, a warp's sums take 2 P(P+1) columns of its lane quadrant).  The last
-// rotation of every output row adds into the sum with its multiply-adds, and
-// the 32 lanes' sums are added in lane order once per target; the list is
-// summed per lane in round order.  `tcols` = tensor-memory columns of the CTA
-// (a power of two >= ceil(warps / 4) * 2 P(P+1)); the launch checks that the
-// CTAs resident on an SM fit in its 512 columns.
+// The lanes' sums, flushed into X, back into tensor memory, with zeros for the
+// lanes for which `zero` is set (all lanes take part: tcgen05.st is collective).
+template <typename T, int P, int N>
+__device__ __forceinline__ void refill_rows(Sw<T> X, uint32_t ta, bool zero) {
+    if constexpr (N < P) {
+        constexpr int o = N * (N + 1), NC = 4 * (N + 1);
+        uint32_t w[NC];
+#pragma unroll
+        for (int k = 0; k < 2 * (N + 1); ++k) tm_put(w + 2 * k, zero ? T(0) : X[o + k]);
+        tm_st<NC>(ta + 2 * o, w);
+        refill_rows<T, P, N + 1>(X, ta, zero);
+    }
+}
+
+// The flushed sums of lanes [lo, hi) added coefficient by coefficient in lane
+// order, stored into dst (added to it when `add`); a null dst sets
+// STATUS_NULL_POINTER.  Ends with a warp barrier (X is free afterwards).
+template <typename T, int S>
+__device__ __forceinline__ void sum_lanes(Sw<T> X, T *dst, int lo, int hi, bool add, int *status) {
+    constexpr int NA = (S + 31) / 32;          // coefficients per lane
+    if (dst == nullptr) {
+        if (X.lane == 0) atomicOr(status, STATUS_NULL_POINTER);
+    } else {
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            const int e = X.lane + a * 32;
+            if (e < S) {
+                T v = T(0);
+                for (int i = lo; i < hi; ++i) v += X.at(e, i);
+                dst[e] = add ? dst[e] + v : v;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Sources [a, b) of target t's list (an inverted range sets STATUS_BAD_OFFSETS
+// and counts as empty).
+__device__ __forceinline__ void list_range(const long long *offsets, long long t, int *status, int lane,
+                                           long long &a, long long &b) {
+    a = offsets[t];
+    b = offsets[t + 1];
+    if (b < a) {
+        if (lane == 0) atomicOr(status, STATUS_BAD_OFFSETS);
+        b = a;
+    }
+}
+
+// FP64 M2L interaction lists, one target per warp at a time, with each lane's
+// running sum of its translations kept in tensor memory (free in this kernel:
+// 256 KB per SM, a warp's sums take 2 P(P+1) columns of its lane quadrant).
+// The last rotation of every output row adds into the sum with its
+// multiply-adds; a target's sums are added across lanes, in lane order, once
+// the list is done.  A warp takes its targets in deal order and packs its
+// rounds: when a list ends k < 32 sources into a round and the warp's next list
+// has at least 32 sources, lanes k..31 of that round already translate the next
+// list's first sources (no lane translates a missing source there).  Lanes
+// k..31 then hand their sums of the ending list to the target before the round
+// (summed, written, and reset to zero) and lanes 0..k-1 theirs after it, so a
+// lane's sum only ever holds one target's translations.  A target's result is
+// deterministic (it depends on the list and on the lengths of the lists dealt
+// to the same warp).  `tcols` = tensor-memory columns of the CTA (a power of
+// two >= ceil(warps / 4) * 2 P(P+1)); the launch checks that the CTAs resident
+// on an SM fit in its 512 columns.
 template <typename T, int P>
 __global__ void __launch_bounds__(256, 1) ulists_acc_kernel(const T *const *src, const T *shift,
                                                             const long long *offsets, T *const *out,
                                                             long long n_targets, int accumulate,
                                                             int *status, int tcols) {
     constexpr int S = P * (P + 1);
-    constexpr int NA = (S + 31) / 32;          // coefficients per lane in the reduction
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     Sw<T> X{reinterpret_cast<T *>(smem_raw) + (size_t)warp * S * XSTRIDE, lane};
@@ -676,50 +731,71 @@ __global__ void __launch_bounds__(256, 1) ulists_acc_kernel(const T *const *src,
     const uint32_t ta = *tslot + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 2 * S);
     const long long nw = (long long)gridDim.x * nwarps;
     const long long w = (long long)blockIdx.x * nwarps + warp;
-    for (long long k = 0; k * nw < n_targets; ++k) {
-        const long long t = deal_chunk(k, nw, w);
-        if (t >= n_targets) continue;
-        long long j0 = offsets[t], j1 = offsets[t + 1];
-        if (j1 < j0) {
-            if (lane == 0) atomicOr(status, STATUS_BAD_OFFSETS);
-            j1 = j0;
+
+    // (only k, t, pos, j1 and the flags live across a round's translation, and
+    // the round has one call site of the translation)
+    long long k = 0;
+    long long t = deal_chunk(0, nw, w);
+    long long j1 = 0, pos = 0;   // end of target t's list, its next source (lane 0's)
+    if (t < n_targets) list_range(offsets, t, status, lane, pos, j1);
+    bool fresh = true;           // the lanes' sums hold nothing yet
+    bool partial = false;        // out[t] already holds part of the result
+    while (t < n_targets) {
+        const long long rem = j1 - pos;
+        long long u0 = 0;        // start of the next list, if it is packed into this round
+        bool pack = false;
+        if (rem > 0 && rem < 32) {
+            const long long tn = deal_chunk(k + 1, nw, w);
+            if (tn < n_targets) {
+                long long u1;
+                list_range(offsets, tn, status, lane, u0, u1);
+                pack = u1 - u0 >= 32;
+            }
         }
-        const int rounds = (int)((j1 - j0 + 31) / 32);
-        for (int r = 0; r < rounds; ++r) {
-            const long long j = j0 + (long long)r * 32 + lane;
-            const T *s = (j < j1) ? src[j] : nullptr;
-            if (j < j1 && s == nullptr) atomicOr(status, STATUS_NULL_POINTER);
+        const int ka = pack ? (int)rem : 32;           // lanes 0..ka-1 on target t
+        if (pack && !fresh) {                          // lanes ka..31 hand over their sums
+            tm_wait_st();
+            flush_rows<T, P, 0>(X, ta);
+            __syncwarp();
+            sum_lanes<T, S>(X, out[t], ka, 32, accumulate, status);
+            refill_rows<T, P, 0>(X, ta, lane >= ka);
+            __syncwarp();                              // X is read before the copies overwrite it
+            partial = true;
+        }
+        if (rem > 0) {                                 // the round
+            const long long j = lane < ka ? pos + lane : u0 + (lane - ka);
+            const bool valid = lane >= ka || j < j1;
+            const T *s = valid ? src[j] : nullptr;
+            if (valid && s == nullptr) atomicOr(status, STATUS_NULL_POINTER);
             load_solids<T, S>(X, s, src);
             __syncwarp();
             T x = T(0), y = T(0), z = T(1);
             if (s) { x = shift[3 * j]; y = shift[3 * j + 1]; z = shift[3 * j + 2]; }
-            if (r > 0) tm_wait_st();                    // the previous round's sums are written
-            translate_u<T, P, OP_M2L, true, true>(X, x, y, z, TAcc{ta, r == 0});
+            if (!fresh) tm_wait_st();                  // earlier writes of the sums are done
+            translate_u<T, P, OP_M2L, true, true>(X, x, y, z, TAcc{ta, fresh});
             __syncwarp();
+            fresh = false;
+            pos += ka;
         }
-        if (rounds > 0) {
-            tm_wait_st();
-            flush_rows<T, P, 0>(X, ta);
-            __syncwarp();
-        }
-        T *dst = out[t];
-        if (dst == nullptr) {
-            if (lane == 0) atomicOr(status, STATUS_NULL_POINTER);
-        } else {
-#pragma unroll
-            for (int a = 0; a < NA; ++a) {
-                const int e = lane + a * 32;
-                if (e < S) {
-                    T v = T(0);
-                    if (rounds > 0) {
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) v += X.at(e, i);
-                    }
-                    dst[e] = accumulate ? dst[e] + v : v;
-                }
+        if (pos >= j1) {                               // target t is done (or its list empty)
+            if (!fresh) {
+                tm_wait_st();
+                flush_rows<T, P, 0>(X, ta);
+                __syncwarp();
             }
+            sum_lanes<T, S>(X, out[t], 0, fresh ? 0 : ka, partial || accumulate, status);
+            ++k;
+            t = deal_chunk(k, nw, w);
+            if (t < n_targets) list_range(offsets, t, status, lane, pos, j1);
+            if (pack) {                                // lanes 0..ka-1 restart at zero; the
+                refill_rows<T, P, 0>(X, ta, lane < ka);   // next list's first 32-ka are done
+                __syncwarp();
+                pos += 32 - ka;
+            } else {
+                fresh = true;
+            }
+            partial = false;
         }
-        __syncwarp();
     }
     tm_wait_st();
     asm volatile("tcgen05.fence::before_thread_sync;");
