@@ -98,11 +98,6 @@ __device__ __forceinline__ double ct<double>(int i) { return c_tab64[i]; }
 template <>
 __device__ __forceinline__ float ct<float>(int i) { return c_tab32[i]; }
 
-// Warp-level fence: keeps the instruction scheduler from hoisting the shared-memory
-// traffic of one row (or column) above the previous one, which would keep
-// several rows alive in registers at once.
-__device__ __forceinline__ void fence() { __syncwarp(); }
-
 // Per-lane view of the warp's solid area: element e of lane j at e*33 + j.
 // The odd stride keeps both access patterns conflict-free (a lane walking its
 // own solid, and the warp copying one solid with consecutive elements per
@@ -149,7 +144,7 @@ struct Powers {
 
 // Input row N: scale, orthonormal basis, rotate alpha, swap, rotate beta, swap.
 template <typename T, int P, int OP, int N>
-__device__ __forceinline__ void rows_in(Sw<T> X, const Powers<T, P> &pw, T s, T step) {
+__device__ __forceinline__ void rows_in(Sw<T> X, const Powers<T, P> &pw, T s) {
     if constexpr (N < P) {
         constexpr int o = N * (N + 1);
         T ar[N + 1], ai[N + 1], br[N + 1], bi[N + 1];
@@ -289,7 +284,7 @@ struct TAcc {
 // multiply-adds (the sums over a target's list are then added across lanes
 // once per target, not once per round).
 template <typename T, int P, int OP, int N, bool ACC = false>
-__device__ __forceinline__ void rows_out(Sw<T> X, const Powers<T, P> &pw, T so, T step, TAcc acc = TAcc{0, true}) {
+__device__ __forceinline__ void rows_out(Sw<T> X, const Powers<T, P> &pw, T so, TAcc acc = TAcc{0, true}) {
     if constexpr (N < P) {
         constexpr int o = N * (N + 1);
         T ar[N + 1], ai[N + 1], br[N + 1], bi[N + 1];
@@ -350,9 +345,9 @@ __device__ __forceinline__ void rows_out(Sw<T> X, const Powers<T, P> &pw, T so, 
 // K - P, 2P <= K < 3P output row K - 2P.
 template <typename T, int P, int OP, int K>
 __device__ __forceinline__ void step_body(Sw<T> X, const Powers<T, P> &pw, T s, T so) {
-    if constexpr (K < P) rows_in<T, P, OP, K>(X, pw, s, T(0));
+    if constexpr (K < P) rows_in<T, P, OP, K>(X, pw, s);
     else if constexpr (K < 2 * P) columns_z<T, P, OP, K - P>(X);
-    else if constexpr (K < 3 * P) rows_out<T, P, OP, K - 2 * P>(X, pw, so, T(0));
+    else if constexpr (K < 3 * P) rows_out<T, P, OP, K - 2 * P>(X, pw, so);
 }
 
 // Paired steps: rows n and P-1-n (columns M and P-1-M) share one step, so
@@ -368,14 +363,14 @@ __device__ __forceinline__ void step_body2(Sw<T> X, const Powers<T, P> &pw, cons
     if constexpr (K < 3 * H) {
         constexpr int ph = K / H, i = K % H, j = P - 1 - i;
         if constexpr (ph == 0) {
-            rows_in<T, P, OP, i>(X, pw, sin[i], T(0));
-            if constexpr (j != i) rows_in<T, P, OP, j>(X, pw, sin[j], T(0));
+            rows_in<T, P, OP, i>(X, pw, sin[i]);
+            if constexpr (j != i) rows_in<T, P, OP, j>(X, pw, sin[j]);
         } else if constexpr (ph == 1) {
             columns_z<T, P, OP, i>(X);
             if constexpr (j != i) columns_z<T, P, OP, j>(X);
         } else {
-            rows_out<T, P, OP, i, ACC>(X, pw, sout[i], T(0), acc);
-            if constexpr (j != i) rows_out<T, P, OP, j, ACC>(X, pw, sout[j], T(0), acc);
+            rows_out<T, P, OP, i, ACC>(X, pw, sout[i], acc);
+            if constexpr (j != i) rows_out<T, P, OP, j, ACC>(X, pw, sout[j], acc);
         }
     }
 }
