@@ -528,3 +528,31 @@ def test_lists_m2l_packed_rounds(sf, orc, h64, accumulate, P):
             each, _ = orc.batch("m2l", P, P, S[src_idx[a:b]], sh[a:b])
             want[i] += each.sum(axis=0)
     U.check_rows(runs[0][pick], want, P, "L", TOL["f64"], what=f"packed lists P={P}")
+
+
+@pytest.fixture(scope="module")
+def h64_max(sf):
+    h = sf.Handle(64, "f64")
+    yield h
+    h.close()
+
+
+@pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
+@pytest.mark.parametrize("P", [48, 64])
+def test_largest_orders(sf, orc, h64_max, op, P):
+    """The largest orders an FP64 handle takes (P_max = 64): the generic kernel
+    with the rotated solid in the global scratch and the powers regenerated
+    per row (three-term recurrence up to m = 63).  M2M / L2L on random solids,
+    M2L on charge expansions (see test_high_orders); every expansion within
+    1e-12 of the oracle."""
+    g = W.rng(2100 + P)
+    count = 6
+    if op == "m2l":
+        C, sh = _charge_expansions(orc, g, count, P, op)
+    else:
+        C = W.random_solids(g, count, P, decay=0.4)
+        sh = W.shifts(g, count, 2.0, 4.0)
+    got = U.run_batch(sf, h64_max, op, C, sh, P, P, "f64")
+    want, _ = orc.batch(op, P, P, C, sh)
+    U.check_rows(got, want, P, U.out_kind(op), TOL["f64"], a=U.out_radius(op, sh),
+                 what=f"{op} P={P}")
