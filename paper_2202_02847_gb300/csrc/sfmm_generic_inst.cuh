@@ -2,6 +2,8 @@
 // type (SFMM_GENERIC_T) and either one op (SFMM_GENERIC_OP) or the
 // multi-class kernel (SFMM_GENERIC_MULTI).  Included by one small translation
 // unit per case, so the units compile in parallel.
+#include <atomic>
+
 #include "sfmm_generic.h"
 #include "sfmm_wide.cuh"
 
@@ -74,16 +76,29 @@ bool wide_launch(const sfmm_ctx *h, int wfix, cudaStream_t stream, const DevTabl
     if (per_warp > h->smem_optin) return false;
     if (count == 0) return true;
     auto k = wide::wbatch_kernel<T, OP>;
+    // block size and resident blocks per SM for (Q, wfix), from the occupancy
+    // calculator once per process (the answer depends only on these and on the
+    // kind of device, which is one per process here; a serving loop launches
+    // this kernel once per chunk)
+    static std::atomic<int> cache[wide::MAXQ + 1][9];
     int best_w = 0, best_nb = 0;
-    for (int w = 8; w >= 1; --w) {
-        if ((size_t)w * per_warp > h->smem_optin || (wfix > 0 && w != wfix)) continue;
-        int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, w * WARP, (size_t)w * per_warp) != cudaSuccess)
-            nb = 0;
-        if (nb > 0 && w * nb > best_w * best_nb) {
-            best_w = w;
-            best_nb = nb;
+    const int key = wfix > 0 && wfix <= 8 ? wfix : 0;
+    const int hit = cache[Q][key].load(std::memory_order_relaxed);
+    if (hit > 0) {
+        best_w = hit / 1024;
+        best_nb = hit % 1024;
+    } else {
+        for (int w = 8; w >= 1; --w) {
+            if ((size_t)w * per_warp > h->smem_optin || (wfix > 0 && w != wfix)) continue;
+            int nb = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, w * WARP, (size_t)w * per_warp) != cudaSuccess)
+                nb = 0;
+            if (nb > 0 && w * nb > best_w * best_nb) {
+                best_w = w;
+                best_nb = nb;
+            }
         }
+        if (best_w >= 1) cache[Q][key].store(best_w * 1024 + best_nb, std::memory_order_relaxed);
     }
     if (best_w < 1) return false;
     const long long groups = (count + wide::Pk<T>::W - 1) / wide::Pk<T>::W;
