@@ -485,38 +485,46 @@ def test_lists_on_two_streams_share_one_handle(sf, h64):
 
 
 @pytest.mark.parametrize("accumulate", [False, True])
-@pytest.mark.parametrize("P", [6, 10])
-def test_lists_m2l_packed_rounds(sf, orc, h64, accumulate, P):
-    """FP64 M2L lists with more targets than warps (every warp takes several
-    lists in turn), lengths 0..80 with many just above and below multiples of
-    32, so that the kernel packs the next list's first sources into the last
-    round of a list (and hands the lanes' sums over around that round).  Every
-    target within 1e-12 of the oracle's sum of its list, and the same bits on
-    a second run."""
+@pytest.mark.parametrize("dtype,P", [("f64", 6), ("f64", 10), ("f64", 12), ("f32", 10)])
+def test_lists_m2l_packed_rounds(sf, orc, h64, h32, accumulate, dtype, P):
+    """M2L lists with more targets than warps (every warp takes several lists
+    in turn), lengths 0..80 with many just above and below multiples of 32, so
+    that the kernels pack the next list's first sources into the last round of
+    a list (FP64 up to order 10: lane sums in tensor memory, handed over around
+    that round; FP64 order 12 and FP32: the round's sum split between the two
+    targets).  Every target within the dtype's tolerance of the oracle's sum
+    of its list, and the same bits on a second run."""
     import torch
-    g = W.rng(7700 + P)
+    g = W.rng(7700 + P + (100 if dtype == "f32" else 0))
     nt = 5000
     lens = g.choice([0, 1, 5, 31, 32, 33, 37, 40, 63, 64, 65, 80], size=nt)
     offs = np.zeros(nt + 1, np.int64)
     np.cumsum(lens, out=offs[1:])
     nnz = int(offs[-1])
     nsrc = 64
-    S = W.random_solids(g, nsrc, P)
+    if dtype == "f32":
+        S, _ = _charge_expansions(orc, g, nsrc, P, "m2l")
+    else:
+        S = W.random_solids(g, nsrc, P)
     src_idx = g.integers(0, nsrc, size=nnz)
     sh = W.shifts(g, nnz)
     init = W.random_solids(g, nt, P)
-    dS = torch.tensor(S, device="cuda")
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    if dtype == "f32":
+        S, sh, init = (a.astype(np.float32).astype(np.float64) for a in (S, sh, init))
+    h = h64 if dtype == "f64" else h32
+    dS = torch.tensor(S, device="cuda", dtype=tdt)
     psrc = sf.pointer_array(dS, P * (P + 1), torch.tensor(src_idx))
-    dsh = torch.tensor(sh, device="cuda")
+    dsh = torch.tensor(sh, device="cuda", dtype=tdt)
     doffs = torch.tensor(offs, device="cuda")
     runs = []
     for _ in range(2):
-        dO = torch.tensor(init, device="cuda")
+        dO = torch.tensor(init, device="cuda", dtype=tdt)
         pout = sf.pointer_array(dO, P * (P + 1), torch.arange(nt))
-        sf.translate_lists(h64, "m2l", psrc, dsh, doffs, pout, P, P, nt, accumulate=accumulate)
+        sf.translate_lists(h, "m2l", psrc, dsh, doffs, pout, P, P, nt, accumulate=accumulate)
         torch.cuda.synchronize()
-        assert h64.sync_status() == 0
-        runs.append(dO.cpu().numpy())
+        assert h.sync_status() == 0
+        runs.append(dO.double().cpu().numpy())
     assert np.array_equal(runs[0], runs[1])
     pick = np.sort(g.choice(nt, size=96, replace=False))
     pick[:4] = [0, 1, nt - 2, nt - 1]
@@ -527,7 +535,7 @@ def test_lists_m2l_packed_rounds(sf, orc, h64, accumulate, P):
         if b > a:
             each, _ = orc.batch("m2l", P, P, S[src_idx[a:b]], sh[a:b])
             want[i] += each.sum(axis=0)
-    U.check_rows(runs[0][pick], want, P, "L", TOL["f64"], what=f"packed lists P={P}")
+    U.check_rows(runs[0][pick], want, P, "L", TOL[dtype], what=f"packed lists {dtype} P={P}")
 
 
 @pytest.fixture(scope="module")
