@@ -725,6 +725,8 @@ def per_order_sweep(orders, dtype, sample=12, seed=900):
             kern = f"ubatch_kernel<{'double' if dtype == 'f64' else 'float'},{P},M2L>"
         elif dtype == "f32" and P >= 16:
             kern = "wbatch_kernel<float, M2L> (warp-cooperative, 4 solids per warp)"
+        elif dtype == "f64" and P >= 30:
+            kern = "wbatch_kernel<double, M2L> (warp-cooperative, 2 solids per warp)"
         else:
             kern = "batch_kernel (generic, per-thread)"
         rec = {"P": P, "count": n, "ms": t * 1e3, "translations_per_s": n / t,

@@ -245,9 +245,10 @@ sfmm_status sfmm_translate_pass(sfmm_handle h, const sfmm_pass_class *classes, i
  * Launch policies (the tile-size choice of Sec. 3.2, made per order on the
  * GPU): which kernel variant serves (op, p_in, p_out) on this handle and how
  * many warps a block has (0 = automatic).
- *   SFMM_POLICY_AUTO     - built-in choice: unrolled if compiled; FP32 batch
- *                          calls the warp-cooperative kernel for M2L of orders
- *                          16..31 and M2M / L2L of orders 22..31; else shared
+ *   SFMM_POLICY_AUTO     - built-in choice: unrolled if compiled; batch calls
+ *                          the warp-cooperative kernel for FP32 M2L of orders
+ *                          16..31, FP32 M2M / L2L of orders 22..31 and FP64
+ *                          M2L of orders 30..31; else shared
  *                          memory while enough warps fit per SM (FP64: two
  *                          blocks of two or more warps; FP32: eight warps);
  *                          else the global scratch (launches that use

@@ -38,7 +38,6 @@ void set_kernel_attrs(size_t smem) {
     cudaFuncSetAttribute(p2x_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-// Copy the host tables into one device buffer converted to T.
 // Transposed copies of the swap and z-translation tables for the
 // warp-cooperative kernels (layout in DevTables).
 struct WideHost {
@@ -82,6 +81,8 @@ WideHost transpose_tables(const HostTables &ht) {
     return w;
 }
 
+// Copy the host tables (and their transposed copies) into one device buffer
+// converted to T.
 template <typename T>
 sfmm_status upload(const HostTables &ht, sfmm_ctx *h, DevTables<T> *dt) {
     const WideHost wh = transpose_tables(ht);
@@ -293,18 +294,20 @@ struct ScratchGuard {
 };
 
 // The warp-cooperative kernel serves a batch call when the policy says so, or
-// under AUTO for FP32 M2L of orders 16..31 and FP32 M2M / L2L of orders
-// 22..31, where it is faster than the per-thread generic kernel with the
-// global scratch (measured on GB300: M2L 0.78 vs 0.86 ms at P = 16, 3.6 vs
-// 6.5 ms at P = 30; M2M / L2L even at P = 20, 1.3x faster at P = 30).  In FP64
-// the per-thread kernels keep the FP64 pipe busier and stay the default.
+// under AUTO where it is faster than the per-thread generic kernel (measured on
+// GB300, 155,648 translations): FP32 M2L of orders 16..31 (0.78 vs 0.86 ms at
+// P = 16, 3.6 vs 6.5 ms at P = 30), FP32 M2M / L2L of orders 22..31 (even at
+// P = 20, 1.3x faster at P = 30), FP64 M2L of orders 30 and 31 (24.5 vs 26.8 ms
+// at P = 30).  Below those orders, and for FP64 M2M / L2L, the per-thread
+// kernels keep the pipes busier.
 template <typename T>
 bool wants_wide(const sfmm_ctx *h, int op, int p_in, int p_out) {
     const int pol = h->policy[op][p_in][p_out];
     if (pol == SFMM_POLICY_WIDE) return true;
     const int Q = p_in > p_out ? p_in : p_out;
-    return pol == SFMM_POLICY_AUTO && sizeof(T) == sizeof(float) && Q <= wide_max_order() &&
-           Q >= (op == OP_M2L ? 16 : 22);
+    if (pol != SFMM_POLICY_AUTO || Q > wide_max_order()) return false;
+    if (sizeof(T) == sizeof(float)) return Q >= (op == OP_M2L ? 16 : 22);
+    return op == OP_M2L && Q >= 30;
 }
 
 template <typename T>
