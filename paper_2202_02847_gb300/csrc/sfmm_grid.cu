@@ -149,7 +149,7 @@ __constant__ unsigned char c_sidx_of_pos[SOLID];
 // The three kernels below give every thread one fixed coefficient (its
 // table entries and scale factor are read once: lanes reading different
 // entries of constant or parameter memory would be serialised) and let the
-// blocks stride over boxes.
+// blocks stride over boxes, four boxes' loads in flight per thread.
 constexpr int SOLID_THREADS = 288;             // SOLID rounded up to whole warps
 
 // largest |x| of the level's sources (float bits of a non-negative float
@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(SOLID_THREADS) xmax_kernel(const double *M, lo
     float v = 0.f;
     if (p < SOLID) {
         const double f = sc.s[c_sidx_of_pos[p]];
+#pragma unroll 4
         for (long long b = blockIdx.x; b < nboxes; b += gridDim.x)
             v = fmaxf(v, fabsf((float)(M[b * SOLID + p] * f)));
     }
@@ -195,6 +196,7 @@ __global__ void __launch_bounds__(KD) pack_kernel(const double *M, int nside, Sc
     const int pos = c_pos_of_e[e];
     const double f = sc.s[c_sidx_of_e[e]];
     const float g = ldexpf(1.f, source_exp(xmax));
+#pragma unroll 4
     for (int blk = blockIdx.x; blk < nbox; blk += gridDim.x) {
         const int hz2 = blk % nh2, hy2 = (blk / nh2) % nh2, hx2 = (blk / (nh2 * nh2)) % nh2;
         const int par = blk / (nh2 * nh2 * nh2);
@@ -220,6 +222,7 @@ __global__ void __launch_bounds__(SOLID_THREADS) unpack_kernel(const double *ypa
     if (p >= SOLID) return;
     const int e = c_e_of_pos[p];
     const double f = e >= 0 ? ldexp(sc.s[c_sidx_of_pos[p]], -row_exp[e] - source_exp(xmax)) : 0.0;
+#pragma unroll 4
     for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
         double v = 0.0;
         if (e >= 0) {
