@@ -191,24 +191,28 @@ __device__ __forceinline__ int source_exp(const unsigned int *xmax) {
 // e of a block writes coefficient e of the halo boxes the block strides over.
 __global__ void __launch_bounds__(KD) pack_kernel(const double *M, int nside, Scales sc,
                                                   const unsigned int *xmax, __half *xhi, __half *xlo) {
-    const int nh2 = (nside + 6) / 2, nbox = 8 * nh2 * nh2 * nh2;
+    const int nh2 = (nside + 6) / 2, nrows = 8 * nh2 * nh2;
     const int e = threadIdx.x;
     const int pos = c_pos_of_e[e];
     const double f = sc.s[c_sidx_of_e[e]];
     const float g = ldexpf(1.f, source_exp(xmax));
+    // blocks stride over rows (parity, hx2, hy2) of the halo grid and walk the
+    // row's nh2 boxes along z, so the index divisions happen once per row
+    for (int row = blockIdx.x; row < nrows; row += gridDim.x) {
+        const int hy2 = row % nh2, hx2 = (row / nh2) % nh2, par = row / (nh2 * nh2);
+        const int hx = 2 * hx2 + ((par >> 2) & 1) - 3, hy = 2 * hy2 + ((par >> 1) & 1) - 3;
+        const bool xy_in = hx >= 0 && hx < nside && hy >= 0 && hy < nside;
+        const long long xy_box = ((long long)hx * nside + hy) * nside;
+        const long long blk0 = (long long)row * nh2;
 #pragma unroll 4
-    for (int blk = blockIdx.x; blk < nbox; blk += gridDim.x) {
-        const int hz2 = blk % nh2, hy2 = (blk / nh2) % nh2, hx2 = (blk / (nh2 * nh2)) % nh2;
-        const int par = blk / (nh2 * nh2 * nh2);
-        const int hx = 2 * hx2 + ((par >> 2) & 1) - 3, hy = 2 * hy2 + ((par >> 1) & 1) - 3,
-                  hz = 2 * hz2 + (par & 1) - 3;
-        float v = 0.f;
-        if (hx >= 0 && hx < nside && hy >= 0 && hy < nside && hz >= 0 && hz < nside) {
-            const long long box_id = ((long long)hx * nside + hy) * nside + hz;
-            v = (float)(M[box_id * SOLID + pos] * f) * g;      // the power of two is exact
+        for (int hz2 = 0; hz2 < nh2; ++hz2) {
+            const int hz = 2 * hz2 + (par & 1) - 3;
+            float v = 0.f;
+            if (xy_in && hz >= 0 && hz < nside)
+                v = (float)(M[(xy_box + hz) * SOLID + pos] * f) * g;   // the power of two is exact
+            const long long i = (blk0 + hz2) * KD + e;
+            split2f(v, xhi + i, xlo + i);
         }
-        const long long i = (long long)blk * KD + e;
-        split2f(v, xhi + i, xlo + i);
     }
 }
 
@@ -900,9 +904,9 @@ sfmm_status sfmm_grid_m2l(sfmm_grid g, double box_size, const void *M, void *L, 
     const long long nb = (long long)ns * ns * ns;
     const int nh2 = (ns + 6) / 2;
     if (cudaMemsetAsync(g->xmax, 0, sizeof(unsigned int), s) != cudaSuccess) return SFMM_ERR_CUDA;
-    const int nhb = 8 * nh2 * nh2 * nh2;
     xmax_kernel<<<(unsigned)(nb < 2048 ? nb : 2048), SOLID_THREADS, 0, s>>>(reinterpret_cast<const double *>(M), nb, sp, g->xmax);
-    pack_kernel<<<nhb < 4096 ? nhb : 4096, KD, 0, s>>>(reinterpret_cast<const double *>(M), ns, sp, g->xmax, g->xhi, g->xlo);
+    const int nrows = 8 * nh2 * nh2;
+    pack_kernel<<<nrows < 4096 ? nrows : 4096, KD, 0, s>>>(reinterpret_cast<const double *>(M), ns, sp, g->xmax, g->xhi, g->xlo);
     // tiles of 4 x 4 x (nt / 16) same-octant targets; one persistent CTA per SM
     // deals the (tile, row half, K half) units round-robin
     GemmArgs a{g->top, g->ypart, ns, g->h->d_status, g->inject_after};
