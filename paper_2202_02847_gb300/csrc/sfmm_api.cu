@@ -83,11 +83,41 @@ WideHost transpose_tables(const HostTables &ht) {
 
 // Copy the host tables (and their transposed copies) into one device buffer
 // converted to T.
+// M2L's swap tables with the basis factors folded in (layout of F and G):
+// F diag(c), G diag(c) (first input swap) and diag(c) F, diag(c) G (last output
+// swap), c_n^l = sqrt((n-l)!(n+l)!) of the row's input index l or output index m.
+struct FoldedHost {
+    std::vector<double> FI, GI, FO, GO;
+};
+
+FoldedHost fold_tables(const HostTables &ht) {
+    FoldedHost f{ht.F, ht.G, ht.F, ht.G};
+    for (int n = 0; n < ht.Pmax; ++n) {
+        const double *cn = ht.c.data() + n * (n + 1) / 2;
+        int i = ht.Frow[n], j = ht.Grow[n];
+        for (int m = 0; m <= n; ++m) {
+            for (int l = (n + m) & 1; l <= n; l += 2, ++i) {
+                f.FI[i] = ht.F[i] * cn[l];
+                f.FO[i] = cn[m] * ht.F[i];
+            }
+            if (m == 0) continue;
+            for (int l = ((n + m) & 1) ? 2 : 1; l <= n; l += 2, ++j) {
+                f.GI[j] = ht.G[j] * cn[l];
+                f.GO[j] = cn[m] * ht.G[j];
+            }
+        }
+    }
+    return f;
+}
+
 template <typename T>
 sfmm_status upload(const HostTables &ht, sfmm_ctx *h, DevTables<T> *dt) {
     const WideHost wh = transpose_tables(ht);
+    constexpr bool fold = sizeof(T) == sizeof(double);
+    const FoldedHost fh = fold ? fold_tables(ht) : FoldedHost{};
     const size_t nF = ht.F.size(), nG = ht.G.size(), nc = ht.c.size(), nT = ht.Tz[0].size();
-    const size_t nreal = nF + nG + 2 * nc + 3 * nT + wh.FT.size() + wh.GT.size() + 3 * nT;
+    const size_t nreal = nF + nG + 2 * nc + 3 * nT + wh.FT.size() + wh.GT.size() + 3 * nT +
+                         (fold ? 2 * (nF + nG) : 0);
     const size_t nint = 4 * (size_t)(ht.Pmax + 1);
     const size_t bytes = nreal * sizeof(T) + nint * sizeof(int) + 256;
     std::vector<unsigned char> host(bytes, 0);
@@ -112,6 +142,7 @@ sfmm_status upload(const HostTables &ht, sfmm_ctx *h, DevTables<T> *dt) {
     const size_t oT0 = put(ht.Tz[0]), oT1 = put(ht.Tz[1]), oT2 = put(ht.Tz[2]);
     const size_t oFT = put(wh.FT), oGT = put(wh.GT);
     const size_t oU0 = put(wh.TzT[0]), oU1 = put(wh.TzT[1]), oU2 = put(wh.TzT[2]);
+    const size_t oFI = put(fh.FI), oGI = put(fh.GI), oFO = put(fh.FO), oGO = put(fh.GO);
     size_t ibyte = (o * sizeof(T) + 15) / 16 * 16;
     int *ip = reinterpret_cast<int *>(host.data() + ibyte);
     std::memcpy(ip, ht.Frow.data(), (ht.Pmax + 1) * sizeof(int));
@@ -139,6 +170,10 @@ sfmm_status upload(const HostTables &ht, sfmm_ctx *h, DevTables<T> *dt) {
     dt->TzT[2] = d + oU2;
     dt->FTrow = di + 2 * (ht.Pmax + 1);
     dt->GTrow = di + 3 * (ht.Pmax + 1);
+    dt->FI = fold ? d + oFI : nullptr;
+    dt->GI = fold ? d + oGI : nullptr;
+    dt->FO = fold ? d + oFO : nullptr;
+    dt->GO = fold ? d + oGO : nullptr;
     dt->Pmax = ht.Pmax;
     return SFMM_OK;
 }

@@ -34,6 +34,11 @@ struct DevTables {
     const T *FT, *GT;
     const int *FTrow, *GTrow;
     const T *TzT[3];
+    // FP64 only (null in FP32, whose range the products leave above order ~25):
+    // M2L's swaps with the basis factors folded in, packed like F and G:
+    // F diag(c), G diag(c) for the first input swap and diag(c) F, diag(c) G for
+    // the last output swap (one multiplication per coefficient fewer per side)
+    const T *FI, *GI, *FO, *GO;
     int Pmax;
 };
 
@@ -142,17 +147,19 @@ __device__ __forceinline__ void swap_class(const T *__restrict__ t, int off0, in
 // non-zeros at l = (n+m)&1, +2, ...; G_n[m] (m >= 1) at l = 1 or 2, +2, ...
 // with n+m+l odd.  The packed tables hold the rows one after the other, so
 // rows of one parity class are a constant stride apart.
+// Fb, Gb: packed tables to use instead of F and G (same layout), e.g. FI, GI.
 template <typename T>
 __device__ __forceinline__ void swap_row(const DevTables<T> &tb, int n, LaneArr<T> in_re,
                                          LaneArr<T> in_im, LaneArr<T> out_re,
-                                         LaneArr<T> out_im, int mmax) {
-    const T *__restrict__ F = tb.F + __ldg(tb.Frow + n);
+                                         LaneArr<T> out_im, int mmax, const T *Fb = nullptr,
+                                         const T *Gb = nullptr) {
+    const T *__restrict__ F = (Fb ? Fb : tb.F) + __ldg(tb.Frow + n);
     const int fe = n / 2 + 1;                  // entries of a row with n+m even (l0 = 0)
     const int fo = (n + 1) / 2;                // entries of a row with n+m odd (l0 = 1)
     const int f0 = (n & 1) ? fo : fe;          // row m = 0
     swap_class(F, 0, fe + fo, n & 1, n, in_re, out_re, 0, mmax);
     swap_class(F, f0, fe + fo, (n + 1) & 1, n, in_re, out_re, 1, mmax);
-    const T *__restrict__ G = tb.G + __ldg(tb.Grow + n);
+    const T *__restrict__ G = (Gb ? Gb : tb.G) + __ldg(tb.Grow + n);
     const int ge = (n + 1) / 2;                // rows with n+m even: l0 = 1
     const int go = n / 2;                      // rows with n+m odd:  l0 = 2
     const int g1 = ((n + 1) & 1) ? go : ge;    // row m = 1
@@ -286,6 +293,7 @@ __device__ void translate_impl(const DevTables<T> &tb, int p_in, int p_out,
                                const T *__restrict__ src, const T *__restrict__ shift,
                                D dst, bool add, LaneArr<T> X, LaneArr<T> buf) {
     const int P = p_in > p_out ? p_in : p_out;
+    constexpr bool FOLD = OP == OP_M2L && sizeof(T) == sizeof(double);
     // lane memory map: X = rotated solid (rows k < p_in, p_in(p_in+1) elements),
     // buf = two complex row buffers (4P), then for P <= PTAB_MAX the powers of
     // e^{i alpha} and e^{i beta} (4P); above, the powers are regenerated per
@@ -336,9 +344,10 @@ __device__ void translate_impl(const DevTables<T> &tb, int p_in, int p_out,
         const T *cf = ((OP == OP_L2L) ? tb.ic : tb.c) + n * (n + 1) / 2;
         const T p2 = row_pow2<T>((OP == OP_L2L) ? -n : n);
         // (b) scale, change to the orthonormal basis, rotate by alpha
+        // (FP64 M2L: the basis factor is folded into the first swap's tables)
         PowSeq<T> pa(ca, sa);
         for (int m = 0; m <= n; ++m) {
-            const T f = basis_factor(s, ldt(cf + m), p2);
+            const T f = FOLD ? s : basis_factor(s, ldt(cf + m), p2);
             const T re = ldd<CG>(row + m) * f, im = ldd<CG>(row + n + 1 + m) * f;
             T pr, pi;
             if constexpr (ptab) { pr = PAre[m]; pi = PAim[m]; } else { pa.next(m, pr, pi); }
@@ -346,7 +355,7 @@ __device__ void translate_impl(const DevTables<T> &tb, int p_in, int p_out,
             Aim[m] = fma_t(re, pi, im * pr);
         }
         // (c) swap x and z
-        swap_row(tb, n, Are, Aim, Bre, Bim, n + 1);
+        swap_row(tb, n, Are, Aim, Bre, Bim, n + 1, FOLD ? tb.FI : nullptr, FOLD ? tb.GI : nullptr);
         // (d) rotate by beta
         PowSeq<T> pb(cb, sb);
         T pr, pi;
@@ -388,14 +397,15 @@ __device__ void translate_impl(const DevTables<T> &tb, int p_in, int p_out,
                 Bim[m] = im * pr - re * pi;
             }
         }
-        swap_row(tb, n, Bre, Bim, Are, Aim, n + 1);
-        // rotate by -alpha, undo the scaling and the basis change, store
+        swap_row(tb, n, Bre, Bim, Are, Aim, n + 1, FOLD ? tb.FO : nullptr, FOLD ? tb.GO : nullptr);
+        // rotate by -alpha, undo the scaling and the basis change (FP64 M2L:
+        // folded into the last swap's tables), store
         const T *cf = ((OP == OP_M2M) ? tb.ic : tb.c) + n * (n + 1) / 2;
         const T p2 = row_pow2<T>((OP == OP_M2M) ? -n : n);
         D orow = dst + n * (n + 1);
         PowSeq<T> pa(ca, sa);
         for (int m = 0; m <= n; ++m) {
-            const T f = basis_factor(so, ldt(cf + m), p2);
+            const T f = FOLD ? so : basis_factor(so, ldt(cf + m), p2);
             const T re = Are[m] * f, im = Aim[m] * f;
             T pr, pi;
             if constexpr (ptab) { pr = PAre[m]; pi = PAim[m]; } else { pa.next(m, pr, pi); }
