@@ -34,6 +34,7 @@ void set_kernel_attrs(size_t smem) {
     set_generic_attrs<T, OP_M2L>(smem);
     set_generic_attrs<T, OP_L2L>(smem);
     set_multi_attrs<T>(smem);
+    set_pass_attrs<T>(smem);
     cudaFuncSetAttribute(p2x_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(p2x_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }

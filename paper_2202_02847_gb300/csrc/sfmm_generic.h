@@ -1,9 +1,9 @@
 // Launches of the generic (runtime-order) translation kernels.  The kernels
-// are heavy to compile, so each (real type, op) and the multi-class kernel of
-// each real type live in a translation unit of their own
-// (sfmm_generic_<type>_<op>.cu, sfmm_generic_<type>_multi.cu, all including
-// sfmm_generic_inst.cuh); the handle code calls them through these
-// declarations.
+// are heavy to compile, so each (real type, op), the multi-class kernel and
+// the phased pass kernel of each real type live in a translation unit of their
+// own (sfmm_generic_<type>_<op>.cu, sfmm_generic_<type>_multi.cu,
+// sfmm_generic_<type>_pass.cu, all including sfmm_generic_inst.cuh); the
+// handle code calls them through these declarations.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -70,5 +70,7 @@ template <typename T, int OP>
 void set_generic_attrs(size_t smem);
 template <typename T>
 void set_multi_attrs(size_t smem);
+template <typename T>
+void set_pass_attrs(size_t smem);
 
 }  // namespace sfmm

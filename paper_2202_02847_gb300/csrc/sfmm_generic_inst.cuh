@@ -1,14 +1,15 @@
 // Definitions of the generic launches, explicitly instantiated for one real
-// type (SFMM_GENERIC_T) and either one op (SFMM_GENERIC_OP) or the
-// multi-class kernel (SFMM_GENERIC_MULTI).  Included by one small translation
+// type (SFMM_GENERIC_T) and either one op (SFMM_GENERIC_OP), the multi-class
+// kernel (SFMM_GENERIC_MULTI) or the phased pass kernel (SFMM_GENERIC_PASS).  Included by one small translation
 // unit per case, so the units compile in parallel.
 #include <atomic>
 
 #include "sfmm_generic.h"
 #include "sfmm_wide.cuh"
 
-#if !defined(SFMM_GENERIC_T) || !(defined(SFMM_GENERIC_OP) || defined(SFMM_GENERIC_MULTI))
-#error "define SFMM_GENERIC_T and SFMM_GENERIC_OP or SFMM_GENERIC_MULTI before including this file"
+#if !defined(SFMM_GENERIC_T) || \
+    !(defined(SFMM_GENERIC_OP) || defined(SFMM_GENERIC_MULTI) || defined(SFMM_GENERIC_PASS))
+#error "define SFMM_GENERIC_T and SFMM_GENERIC_OP, SFMM_GENERIC_MULTI or SFMM_GENERIC_PASS before including this file"
 #endif
 
 namespace sfmm {
@@ -156,6 +157,10 @@ void set_generic_attrs(size_t smem) {
 template <typename T>
 void set_multi_attrs(size_t smem) {
     attr(multi_lists_kernel<T>, smem);
+}
+
+template <typename T>
+void set_pass_attrs(size_t smem) {
     attr(pass_kernel<T>, smem);
 }
 
@@ -174,12 +179,15 @@ template void glists_launch<GT, GOP>(const sfmm_ctx *, const Geometry &, cudaStr
 template bool wide_launch<GT, GOP>(const sfmm_ctx *, int, cudaStream_t, const DevTables<GT> &,
                                    const GT *const *, GT *const *, const GT *, int, int, long long, int, int *);
 template void set_generic_attrs<GT, GOP>(size_t);
-#else
+#elif defined(SFMM_GENERIC_MULTI)
 using GT = SFMM_GENERIC_T;
 template void multi_launch<GT>(const sfmm_ctx *, const Geometry &, cudaStream_t, const DevTables<GT> &,
                                const MultiParams &, const GT *const *, const GT *, const long long *,
                                GT *const *, int, GT *, int *);
 template void set_multi_attrs<GT>(size_t);
+#else
+using GT = SFMM_GENERIC_T;
+template void set_pass_attrs<GT>(size_t);
 template cudaError_t pass_launch<GT>(const sfmm_ctx *, const Geometry &, cudaStream_t, const DevTables<GT> &,
                                      const PassParams &, GT *, unsigned long long *, int *);
 template long long pass_resident_blocks<GT>(const sfmm_ctx *, const Geometry &);

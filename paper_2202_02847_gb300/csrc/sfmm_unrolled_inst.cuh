@@ -1,12 +1,20 @@
 // Instantiation of the unrolled kernels for one order (SFMM_UNROLLED_P) and
 // one real type (SFMM_UNROLLED_T).  Included by one small translation unit per
-// (order, type), so the units compile in parallel.
+// (order, type), so the units compile in parallel; the largest order's units
+// are split further by SFMM_UNROLLED_PART (1: the batch kernels, 2: the lists
+// kernels; 0, the default: both), each part a module with its own copy of the
+// constant tables (fill for the batch part, fill_lists for the lists part).
 #include "sfmm_unrolled.cuh"
 #include "sfmm_unrolled_dispatch.h"
 
 #if !defined(SFMM_UNROLLED_P) || !defined(SFMM_UNROLLED_T) || !defined(SFMM_UNROLLED_NS)
 #error "define SFMM_UNROLLED_P, SFMM_UNROLLED_T and SFMM_UNROLLED_NS before including this file"
 #endif
+#ifndef SFMM_UNROLLED_PART
+#define SFMM_UNROLLED_PART 0
+#endif
+#define SFMM_WITH_BATCH (SFMM_UNROLLED_PART != 2)
+#define SFMM_WITH_LISTS (SFMM_UNROLLED_PART != 1)
 
 namespace sfmm {
 namespace unrolled {
@@ -17,7 +25,8 @@ constexpr int S = P * (P + 1);
 
 using Real = SFMM_UNROLLED_T;
 
-bool fill(const double *t64, const float *t32) {
+// this module's copy of the constant tables
+static bool fill_module(const double *t64, const float *t32) {
     if (std::is_same<Real, double>::value)
         return cudaMemcpyToSymbol(c_tab64, t64, sizeof(double) * NTAB) == cudaSuccess;
     return cudaMemcpyToSymbol(c_tab32, t32, sizeof(float) * NTAB) == cudaSuccess;
@@ -28,18 +37,27 @@ void attr(K k, size_t smem) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <typename T>
-void set_attrs_t(size_t smem) {
-    attr(ubatch_kernel<T, P, OP_M2M>, smem);
-    attr(ubatch_kernel<T, P, OP_M2L>, smem);
-    attr(ubatch_kernel<T, P, OP_L2L>, smem);
-    attr(ulists_kernel<T, P, OP_M2M, 8>, smem);
-    attr(ulists_kernel<T, P, OP_M2L, 32>, smem);
-    attr(ulists_kernel<T, P, OP_L2L, 8>, smem);
-    if constexpr (sizeof(T) == 8 && P <= 10) attr(ulists_acc_kernel<T, P>, smem);
+#if SFMM_WITH_BATCH
+bool fill(const double *t64, const float *t32) { return fill_module(t64, t32); }
+void set_attrs(size_t smem) {
+    attr(ubatch_kernel<Real, P, OP_M2M>, smem);
+    attr(ubatch_kernel<Real, P, OP_M2L>, smem);
+    attr(ubatch_kernel<Real, P, OP_L2L>, smem);
 }
-
-void set_attrs(size_t smem) { set_attrs_t<Real>(smem); }
+#endif
+#if SFMM_WITH_LISTS
+#if SFMM_UNROLLED_PART == 2
+bool fill_lists(const double *t64, const float *t32) { return fill_module(t64, t32); }
+#else
+bool fill_lists(const double *, const float *) { return true; }   // the batch part's module
+#endif
+void set_attrs_lists(size_t smem) {
+    attr(ulists_kernel<Real, P, OP_M2M, 8>, smem);
+    attr(ulists_kernel<Real, P, OP_M2L, 32>, smem);
+    attr(ulists_kernel<Real, P, OP_L2L, 8>, smem);
+    if constexpr (sizeof(Real) == 8 && P <= 10) attr(ulists_acc_kernel<Real, P>, smem);
+}
+#endif
 
 // warps per block and blocks for `chunks` warp-chunks of work
 // (the block size that leaves the most warps resident per SM: with FP32
@@ -78,6 +96,7 @@ bool geometry(K kernel, const Launch &L, long long chunks, int *warps, size_t *s
     return *blocks >= 1;
 }
 
+#if SFMM_WITH_BATCH
 template <typename T, int OP>
 bool batch_t(const void *const *in, void *const *out, const void *shift, long long count,
              int accumulate, const Launch &L) {
@@ -92,6 +111,9 @@ bool batch_t(const void *const *in, void *const *out, const void *shift, long lo
     return cudaGetLastError() == cudaSuccess;
 }
 
+#endif
+
+#if SFMM_WITH_LISTS
 // FP64 M2L lists with the lanes' running sums in tensor memory (orders up to
 // 10, where a warp's sums take at most 220 columns): launched when the
 // resident CTAs of an SM fit in its 512 columns, else false.
@@ -141,6 +163,9 @@ bool lists_t(const void *const *src, const void *shift, const long long *offsets
     return cudaGetLastError() == cudaSuccess;
 }
 
+#endif
+
+#if SFMM_WITH_BATCH
 bool batch(int op, const void *const *in, void *const *out, const void *shift, long long count,
            int accumulate, const Launch &L) {
     if (op == OP_M2M) return batch_t<Real, OP_M2M>(in, out, shift, count, accumulate, L);
@@ -148,12 +173,17 @@ bool batch(int op, const void *const *in, void *const *out, const void *shift, l
     return batch_t<Real, OP_L2L>(in, out, shift, count, accumulate, L);
 }
 
+#endif
+
+#if SFMM_WITH_LISTS
 bool lists(int op, const void *const *src, const void *shift, const long long *offsets,
            void *const *out, long long n_targets, int accumulate, const Launch &L) {
     if (op == OP_M2M) return lists_t<Real, OP_M2M, 8>(src, shift, offsets, out, n_targets, accumulate, L);
     if (op == OP_M2L) return lists_t<Real, OP_M2L, 32>(src, shift, offsets, out, n_targets, accumulate, L);
     return lists_t<Real, OP_L2L, 8>(src, shift, offsets, out, n_targets, accumulate, L);
 }
+
+#endif
 
 }  // namespace SFMM_UNROLLED_NS
 }  // namespace unrolled

@@ -1,5 +1,7 @@
-// Unrolled translation kernels for order P = 12 in double (see sfmm_unrolled.cuh).
+// Unrolled batch kernels for order P = 12 in double (see sfmm_unrolled.cuh; the
+// lists kernels of this order compile in sfmm_unrolled_p12_f64_lists.cu).
 #define SFMM_UNROLLED_P 12
 #define SFMM_UNROLLED_T double
 #define SFMM_UNROLLED_NS p12_f64
+#define SFMM_UNROLLED_PART 1
 #include "sfmm_unrolled_inst.cuh"

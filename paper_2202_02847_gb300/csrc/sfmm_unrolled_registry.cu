@@ -8,7 +8,9 @@ namespace unrolled {
 #define SFMM_DECLARE(NS)                                                                        \
     namespace NS {                                                                              \
     bool fill(const double *, const float *);                                                   \
+    bool fill_lists(const double *, const float *);                                             \
     void set_attrs(size_t);                                                                     \
+    void set_attrs_lists(size_t);                                                               \
     bool batch(int, const void *const *, void *const *, const void *, long long, int,           \
                const Launch &);                                                                 \
     bool lists(int, const void *const *, const void *, const long long *, void *const *,        \
@@ -28,21 +30,26 @@ bool compiled(int P) { return P == 6 || P == 8 || P == 10 || P == 12; }
 
 int table_size() { return NTAB; }
 
+// every module's copy of the constant tables (the order-12 units are split in a
+// batch module and a lists module, see sfmm_unrolled_inst.cuh)
+#define SFMM_FILL(NS) (NS::fill(t64, t32) && NS::fill_lists(t64, t32))
 bool fill_constants(const double *t64, const float *t32) {
-    return p6_f64::fill(t64, t32) && p8_f64::fill(t64, t32) && p10_f64::fill(t64, t32) &&
-           p12_f64::fill(t64, t32) && p6_f32::fill(t64, t32) && p8_f32::fill(t64, t32) &&
-           p10_f32::fill(t64, t32) && p12_f32::fill(t64, t32);
+    return SFMM_FILL(p6_f64) && SFMM_FILL(p8_f64) && SFMM_FILL(p10_f64) && SFMM_FILL(p12_f64) &&
+           SFMM_FILL(p6_f32) && SFMM_FILL(p8_f32) && SFMM_FILL(p10_f32) && SFMM_FILL(p12_f32);
 }
+#undef SFMM_FILL
 
 void set_attributes(size_t smem) {
-    p6_f64::set_attrs(smem);
-    p8_f64::set_attrs(smem);
-    p10_f64::set_attrs(smem);
-    p12_f64::set_attrs(smem);
-    p6_f32::set_attrs(smem);
-    p8_f32::set_attrs(smem);
-    p10_f32::set_attrs(smem);
-    p12_f32::set_attrs(smem);
+#define SFMM_ATTRS(NS) NS::set_attrs(smem); NS::set_attrs_lists(smem);
+    SFMM_ATTRS(p6_f64)
+    SFMM_ATTRS(p8_f64)
+    SFMM_ATTRS(p10_f64)
+    SFMM_ATTRS(p12_f64)
+    SFMM_ATTRS(p6_f32)
+    SFMM_ATTRS(p8_f32)
+    SFMM_ATTRS(p10_f32)
+    SFMM_ATTRS(p12_f32)
+#undef SFMM_ATTRS
 }
 
 #define SFMM_PICK(P, F64, CALL)                                 \
