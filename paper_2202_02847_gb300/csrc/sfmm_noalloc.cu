@@ -107,7 +107,6 @@ extern "C" sfmm_status sfmm_translate_batch_noalloc(sfmm_handle h, sfmm_op op,
                                                     const void *shift, int p_in, int p_out,
                                                     long long count, int accumulate,
                                                     sfmm_stream stream) {
-    SfmmRange nvtx_range("sfmm_translate_batch_noalloc");
     if (h == nullptr || count < 0) return SFMM_ERR_ARG;
     if (op != SFMM_M2M && op != SFMM_M2L && op != SFMM_L2L) return SFMM_ERR_ARG;
     if (p_in < 1 || p_out < 1 || p_in > h->Pmax || p_out > h->Pmax) return SFMM_ERR_ORDER;
