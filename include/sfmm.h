@@ -258,7 +258,8 @@ sfmm_status sfmm_translate_pass(sfmm_handle h, const sfmm_pass_class *classes, i
  *                          that event, so a captured graph is not ordered
  *                          against other work on the same handle: give each
  *                          graph a handle of its own)
- *   SFMM_POLICY_UNROLLED - fixed-order kernel; only p_in = p_out in {6,8,10,12}
+ *   SFMM_POLICY_UNROLLED - fixed-order kernel; only p_in = p_out in
+ *                          {4,5,6,7,8,9,10,12}
  *   SFMM_POLICY_SHARED   - generic kernel, working set in shared memory
  *   SFMM_POLICY_GLOBAL   - generic kernel, rotated solid in the global scratch
  *   SFMM_POLICY_WIDE     - warp-cooperative kernel (a warp translates 4 FP32 or

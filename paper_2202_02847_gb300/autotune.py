@@ -32,7 +32,7 @@ class Autotuner:
                 self.cache = json.load(f)
 
     def candidates(self, p_in, p_out):
-        c = [("unrolled", 0)] if (p_in == p_out and p_in in (6, 8, 10, 12)) else []
+        c = [("unrolled", 0)] if (p_in == p_out and p_in in sfmm.UNROLLED_ORDERS) else []
         c += [("shared", w) for w in (1, 2, 4, 8)]
         c += [("global", w) for w in (1, 2, 4)]
         return c

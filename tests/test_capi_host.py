@@ -41,6 +41,21 @@ def test_every_declared_symbol_is_exported(sf):
         assert hasattr(sf._lib, n), f"{n} declared in include/ but not exported"
 
 
+def test_unrolled_orders_match_the_compiled_units(sf):
+    """sfmm.UNROLLED_ORDERS (what bench, autotuner and tests take as the
+    orders with unrolled kernels) is the registry's list of compiled orders,
+    and each of them has a translation unit per real type."""
+    csrc = os.path.join(ROOT, "paper_2202_02847_gb300", "csrc")
+    reg = open(os.path.join(csrc, "sfmm_unrolled_registry.cu")).read()
+    line = re.search(r"#define SFMM_UNROLLED_ORDERS\(X\)(.*)", reg).group(1)
+    orders = tuple(int(v) for v in re.findall(r"X\((\d+)\)", line))
+    assert orders == sf.UNROLLED_ORDERS
+    units = os.listdir(csrc)
+    for P in orders:
+        for t in ("f64", "f32"):
+            assert f"sfmm_unrolled_p{P}_{t}.cu" in units, (P, t)
+
+
 def test_status_strings(sf):
     for code, name in sf.STATUS.items():
         assert sf.status_string(code).startswith(name)
