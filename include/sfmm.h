@@ -245,7 +245,9 @@ sfmm_status sfmm_translate_pass(sfmm_handle h, const sfmm_pass_class *classes, i
  * Launch policies (the tile-size choice of Sec. 3.2, made per order on the
  * GPU): which kernel variant serves (op, p_in, p_out) on this handle and how
  * many warps a block has (0 = automatic).
- *   SFMM_POLICY_AUTO     - built-in choice: unrolled if compiled; batch calls
+ *   SFMM_POLICY_AUTO     - built-in choice: unrolled if compiled (not for
+ *                          FP64 batch calls of order 12, where the generic
+ *                          kernel below is faster); batch calls
  *                          the warp-cooperative kernel for FP32 M2L of orders
  *                          16..31, FP32 M2M / L2L of orders 22..31 and FP64
  *                          M2L of orders 30..31; else shared
@@ -258,8 +260,7 @@ sfmm_status sfmm_translate_pass(sfmm_handle h, const sfmm_pass_class *classes, i
  *                          that event, so a captured graph is not ordered
  *                          against other work on the same handle: give each
  *                          graph a handle of its own)
- *   SFMM_POLICY_UNROLLED - fixed-order kernel; only p_in = p_out in
- *                          {4,5,6,7,8,9,10,12}
+ *   SFMM_POLICY_UNROLLED - fixed-order kernel; only p_in = p_out <= 12
  *   SFMM_POLICY_SHARED   - generic kernel, working set in shared memory
  *   SFMM_POLICY_GLOBAL   - generic kernel, rotated solid in the global scratch
  *   SFMM_POLICY_WIDE     - warp-cooperative kernel (a warp translates 4 FP32 or

@@ -3,9 +3,9 @@
 #include "sfmm_unrolled_dispatch.h"
 
 // The orders with a unit per real type (sfmm_unrolled_p<P>_{f64,f32}.cu; the
-// order-12 units are split in a batch module and a lists module, see
-// sfmm_unrolled_inst.cuh).
-#define SFMM_UNROLLED_ORDERS(X) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(12)
+// units of orders 11 and 12 are split in a batch module and a lists module,
+// see sfmm_unrolled_inst.cuh).
+#define SFMM_UNROLLED_ORDERS(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
 
 namespace sfmm {
 namespace unrolled {

@@ -191,7 +191,7 @@ POLICY = {"auto": 0, "unrolled": 1, "shared": 2, "global": 3, "wide": 4}
 # Orders p_in = p_out with fully unrolled kernels in libsfmm.so (one unit per
 # order and real type, listed in csrc/sfmm_unrolled_registry.cu); AUTO takes
 # them for these orders, SFMM_POLICY_UNROLLED accepts only these.
-UNROLLED_ORDERS = (4, 5, 6, 7, 8, 9, 10, 12)
+UNROLLED_ORDERS = (1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12)
 
 
 def translate_lists_multi(h, classes, src, shift, offsets, out, accumulate=False, stream=None):

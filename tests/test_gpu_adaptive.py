@@ -133,7 +133,7 @@ def test_graph_capture_replays_the_pass(setup):
 def test_policy_errors(setup):
     sfmm, ap, pts, q, tree, P_node, h = setup
     with pytest.raises(sfmm.SfmmError) as e:
-        sfmm.set_policy(h, "m2l", 11, 11, "unrolled")   # order 11: no unrolled kernels
+        sfmm.set_policy(h, "m2l", 13, 13, "unrolled")   # order 13: no unrolled kernels
     assert e.value.code == 6
     with pytest.raises(sfmm.SfmmError) as e:
         sfmm.set_policy(h, "m2l", 7, 99, "shared")

@@ -129,7 +129,7 @@ def test_high_orders(sf, orc, h64, op, P):
                  what=f"{op} P={P}")
 
 
-@pytest.mark.parametrize("P", [7, 10, 11])
+@pytest.mark.parametrize("P", [7, 10, 12])
 @pytest.mark.parametrize("count", [1, 31, 33, 257])
 def test_ragged_counts(sf, orc, h64, count, P):
     g = W.rng(3000 + count)
@@ -140,11 +140,32 @@ def test_ragged_counts(sf, orc, h64, count, P):
     U.check_rows(got, want, P, "L", TOL["f64"], what=f"m2l count={count}")
 
 
+@pytest.mark.parametrize("policy", ["shared", "global"])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
+@pytest.mark.parametrize("P", [3, 8, 11])
+def test_generic_kernels_at_unrolled_orders(sf, orc, dtype, op, P, policy):
+    """The generic batch kernels at equal orders <= 12, where AUTO takes the
+    unrolled ones (reached by sfmm_set_policy, as the autotuner does): each
+    expansion against the oracle on charge-cluster inputs, 70 translations."""
+    g = W.rng(5700 + 10 * P + len(op))
+    C, sh = _charge_expansions(orc, g, 70, P, op)
+    if dtype == "f32":
+        C, sh = (a.astype(np.float32).astype(np.float64) for a in (C, sh))
+    h = sf.Handle(P, dtype)
+    sf.set_policy(h, op, P, P, policy)
+    got = U.run_batch(sf, h, op, C, sh, P, P, dtype)
+    h.close()
+    want, _ = orc.batch(op, P, P, C, sh)
+    U.check_rows(got, want, P, U.out_kind(op), TOL[dtype], a=U.out_radius(op, sh),
+                 what=f"{dtype} {op} P={P} {policy}")
+
+
 def test_count_zero_is_noop(sf, h64):
     sf.m2l_batch(h64, 0, 0, 0, 4, 4, 0)
 
 
-@pytest.mark.parametrize("P", [9, 10, 11])
+@pytest.mark.parametrize("P", [9, 10, 12])
 @pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
 def test_special_shifts(sf, orc, h64, op, P):
     """Shifts along +z and -z (rho = 0, cos(alpha) = 1 by the special case of
@@ -218,7 +239,7 @@ def test_fp32(sf, orc, h32_30, op, P):
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
-@pytest.mark.parametrize("P", [4, 5, 7, 9])
+@pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 7, 9, 11])
 def test_unrolled_batch_orders(sf, orc, h64, h32_30, dtype, op, P):
     """Batch calls at the low and odd orders with unrolled kernels (AUTO takes
     them), on the expansions of charge clusters in both precisions, each
@@ -290,7 +311,7 @@ def _run_lists(sf, orc, h, op, P_in, P_out, accumulate, seed, dtype="f64", maxle
 
 @pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
 @pytest.mark.parametrize("accumulate", [False, True])
-@pytest.mark.parametrize("P", [4, 5, 6, 7, 8, 9, 10, 12])
+@pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12])
 def test_lists_fixed_orders(sf, orc, h64, op, accumulate, P):
     """Lists at the orders with fully unrolled kernels (groups of 8 or 32 lanes
     per target, lengths 0..70 so that targets take several rounds)."""
@@ -299,14 +320,14 @@ def test_lists_fixed_orders(sf, orc, h64, op, accumulate, P):
 
 
 @pytest.mark.parametrize("op", ["m2m", "m2l", "l2l"])
-@pytest.mark.parametrize("P", [4, 5, 6, 7, 8, 9, 10, 12])
+@pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12])
 def test_lists_fixed_orders_fp32(sf, orc, h32, op, P):
     err = _run_lists(sf, orc, h32, op, P, P, False, 6200 + P, dtype="f32")
     assert err.max() <= TOL["f32"], (int(err.argmax()), err.max())
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("P", [4, 5, 6, 7, 8, 9, 10, 12])
+@pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12])
 def test_lists_m2l_special_shifts(sf, orc, h64, h32, dtype, P):
     """The interaction-list M2L kernel (paired row and column steps, basis
     factors folded into its swap tables) on shifts along +z and -z (rho = 0,
