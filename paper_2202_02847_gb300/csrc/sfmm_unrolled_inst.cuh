@@ -51,11 +51,16 @@ bool fill_lists(const double *t64, const float *t32) { return fill_module(t64, t
 #else
 bool fill_lists(const double *, const float *) { return true; }   // the batch part's module
 #endif
+// (a template, so that the FP32 units never name ulists_acc_kernel<float, P>)
+template <typename R>
+void set_attrs_acc(size_t smem) {
+    if constexpr (sizeof(R) == 8 && P <= 10) attr(ulists_acc_kernel<R, P>, smem);
+}
 void set_attrs_lists(size_t smem) {
     attr(ulists_kernel<Real, P, OP_M2M, 8>, smem);
     attr(ulists_kernel<Real, P, OP_M2L, 32>, smem);
     attr(ulists_kernel<Real, P, OP_L2L, 8>, smem);
-    if constexpr (sizeof(Real) == 8 && P <= 10) attr(ulists_acc_kernel<Real, P>, smem);
+    set_attrs_acc<Real>(smem);
 }
 #endif
 
