@@ -42,7 +42,7 @@ def test_two_ranks_weak_scaling():
     import __graft_entry__
     __graft_entry__.build_library()
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()      # no fork of this (threaded) process
     out = mgr.dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     r0, r1 = out[0], out[1]
